@@ -1,0 +1,172 @@
+/*
+ * sft.h -- C ABI of the GB300 (sm_103a) sparse FastTucker SGD library.
+ *
+ * The library runs the hot path of cuFasterTucker (arXiv 2210.06014) in the
+ * "reusable intermediates, COO storage" form the paper calls
+ * cuFasterTucker_COO (Section "Experimental Settings"):
+ *
+ *   sft_refresh_C       C^(n) = A^(n) B^(n)             Algorithm 3; Algorithm 2
+ *   sft_update_factors  SGD pass over A^(n)             Algorithm 4; Eq. (9), (10)
+ *   sft_update_core     SGD pass over B^(n)             Algorithm 5; Eq. (9), (11)
+ *   sft_loss            sum of squared / absolute       Section "Real-world accuracy"
+ *                       residuals over a set            (test RMSE and MAE)
+ *
+ * Notation: a tensor of order N with mode lengths I_n, factor matrices
+ * A^(n) (I_n x J_n), Kruskal-form core matrices B^(n) (J_n x R), cached
+ * products C^(n) = A^(n) B^(n) (I_n x R).  A nonzero s has coordinates
+ * (i_0 .. i_{N-1}) and value x_s; its prediction is
+ *   x^_s = sum_r prod_k C^(k)[i_k][r]                    (Eq. (1) through Eq. (12)).
+ *
+ * Memory: every array is a *device* pointer owned by the caller (e.g. torch
+ * tensors); the library borrows them and frees nothing it did not allocate.
+ * Matrices are dense row-major float32, 16-byte aligned, with no padding:
+ * A[n] has I_n*J_n elements, B[n] J_n*R, C[n] I_n*R.  A COO set is given as
+ * N device pointers idx[k] (int32, nnz entries each, 0 <= idx[k][s] < I_k) and
+ * val (float32, nnz entries).  An optional permutation perm (uint32, nnz
+ * entries, a permutation of 0..nnz-1) gives the order in which the nonzeros
+ * are visited; NULL means storage order.
+ *
+ * Asynchrony: every call except sft_loss, sft_sync and sft_destroy only
+ * enqueues kernels on the configured CUDA stream and returns.  Argument errors
+ * are detected on the host before anything is launched (SFT_EINVAL).  Bad
+ * data found by a kernel (an index out of range, a permutation entry >= nnz) is
+ * skipped by that kernel and recorded in a device flag that sft_sync and
+ * sft_loss report as SFT_EINVAL.  No call aborts, throws or hangs: sft_sync
+ * gives up after its timeout with SFT_ETIMEOUT.
+ *
+ * Supported shapes on the CUDA path: 2 <= N <= 16, R in {4, 8, 16, 32},
+ * J_n in {4, 8, 16, 32} with 4*J_n >= R, I_n < 2^31, nnz < 2^31.  Other shapes
+ * return SFT_ENOTSUP.
+ */
+#ifndef SFT_H
+#define SFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFT_MAX_ORDER 16
+
+typedef struct sft_ctx sft_ctx; /* opaque; created by sft_init, freed by sft_destroy */
+
+typedef enum {
+    SFT_OK = 0,
+    SFT_EINVAL = 1,   /* bad argument, or bad data flagged by a kernel */
+    SFT_ENOMEM = 2,   /* workspace too small / host allocation failed */
+    SFT_ECUDA = 3,    /* a CUDA runtime call failed (message in sft_last_error) */
+    SFT_ETIMEOUT = 4, /* sft_sync gave up before the stream drained */
+    SFT_ENOTSUP = 5   /* shape or mode not supported by the CUDA path */
+} sft_status;
+
+typedef enum {
+    SFT_FP32 = 0, /* A, B, C float32 */
+    SFT_BF16 = 1  /* reserved: C and a shadow of A in bfloat16 (not yet supported) */
+} sft_precision;
+
+typedef struct {
+    int32_t order;         /* N, 2..16 */
+    const int64_t *dims;   /* host array [N]: I_n */
+    const int32_t *J;      /* host array [N]: J_n */
+    int32_t R;             /* Kruskal rank of the core */
+    int32_t prec;          /* sft_precision */
+    int32_t deterministic; /* 1: minibatch rule with fixed-order sums (bitwise
+                              reproducible, matches the FP64 oracle);
+                              0: Hogwild factor rows (Algorithm 4 style) */
+    void *stream;          /* cudaStream_t to enqueue on (NULL = legacy stream) */
+} sft_config;
+
+/* Bytes of device workspace sft_init needs for this configuration when no
+ * minibatch is larger than max_batch.  Returns 0 for an invalid config. */
+size_t sft_workspace_bytes(const sft_config *cfg, int64_t max_batch);
+
+/* Create a context.  A, B, C: host arrays of N device pointers (see header
+ * comment for layout).  A_lo must be NULL (reserved for the bf16 shadow).
+ * workspace: device buffer of at least sft_workspace_bytes(cfg, max_batch)
+ * bytes, 256-byte aligned, owned by the caller and not touched by anyone else
+ * while the context lives.  The context copies cfg and the pointer arrays.
+ * On success *out receives the context; on failure *out is NULL. */
+sft_status sft_init(const sft_config *cfg, float *const *A, float *const *B, void *const *C,
+                    void *const *A_lo, void *workspace, size_t workspace_bytes, sft_ctx **out);
+
+/* C^(mode) = A^(mode) B^(mode) (Algorithm 3); mode = -1 refreshes every mode.
+ * The caller refreshes a mode after each pass over it, as Algorithm 2 does. */
+sft_status sft_refresh_C(sft_ctx *ctx, int32_t mode);
+
+/* One SGD pass over A^(mode) (Algorithm 2, factor module; Eq. (9)-(10)).
+ * For each visited nonzero s: p_r = prod_{k != mode} C^(k)[i_k][r],
+ * v = B^(mode) p, e = x_s - a_{i_mode} . v, and the row moves by
+ * lr * (e v - lambda a_{i_mode}).
+ *   deterministic = 1: the visit order is cut into minibatches of `batch`
+ *     samples (last one shorter); inside a minibatch every prediction uses the
+ *     rows as they stood at its start and the terms of a repeated row are summed
+ *     (no 1/batch factor).  batch must be <= min(max_batch, 16384).
+ *   deterministic = 0: every nonzero reads its row and adds its own term at
+ *     once with atomic adds, many nonzeros concurrently (Hogwild); `batch` is
+ *     ignored.
+ * C^(mode) is not read and not refreshed. */
+sft_status sft_update_factors(sft_ctx *ctx, int32_t mode, const int32_t *const *idx,
+                              const float *val, const uint32_t *perm, int64_t nnz, int64_t batch,
+                              float lr, float lambda);
+
+/* One SGD pass over B^(mode) (Algorithm 2, core module; Eq. (9), (11)).
+ * For each minibatch of `batch` samples (last one shorter, size M_b), with
+ * B^(mode) as it stood at its start: G = sum_s e_s a_{i_mode(s)} p_s^T and
+ * B^(mode) += lr * (G / M_b - lambda B^(mode)).  batch = nnz gives the single
+ * update per pass of Algorithm 5.  Sums are in a fixed order in both modes.
+ * batch must be <= max_batch or equal to nnz. */
+sft_status sft_update_core(sft_ctx *ctx, int32_t mode, const int32_t *const *idx,
+                           const float *val, const uint32_t *perm, int64_t nnz, int64_t batch,
+                           float lr, float lambda);
+
+/* Sum of squared and of absolute residuals x_s - sum_r prod_k C^(k)[i_k][r]
+ * over the nnz nonzeros, accumulated in float64 in a fixed order.  sse/sae are
+ * HOST pointers; the call waits for the stream and also reports any bad-data
+ * flag raised by earlier kernels. */
+sft_status sft_loss(sft_ctx *ctx, const int32_t *const *idx, const float *val, int64_t nnz,
+                    double *sse, double *sae);
+
+/* As sft_loss, but writes {sse, sae} to the DEVICE buffer out2 (two doubles)
+ * and does not wait. */
+sft_status sft_loss_async(sft_ctx *ctx, const int32_t *const *idx, const float *val, int64_t nnz,
+                          double *out2);
+
+/* Predictions x^_s = sum_r prod_k C^(k)[i_k][r] (Eq. (1) via Eq. (12)) for
+ * the nnz nonzeros, written to the DEVICE array out (float32, nnz entries).
+ * Enqueues only.  Used to fill in missing entries once the model is fitted. */
+sft_status sft_predict(sft_ctx *ctx, const int32_t *const *idx, int64_t nnz, float *out);
+
+/* One epoch of Algorithm 2: for every mode a factor pass then a refresh of
+ * that mode, then for every mode a core pass then a refresh.  perm_factor /
+ * perm_core: host arrays of N device permutation pointers (or NULL for storage
+ * order everywhere; individual entries may be NULL).  Enqueues only. */
+sft_status sft_epoch(sft_ctx *ctx, const int32_t *const *idx, const float *val, int64_t nnz,
+                     const uint32_t *const *perm_factor, const uint32_t *const *perm_core,
+                     int64_t batch_factor, int64_t batch_core, float lr_A, float lambda_A,
+                     float lr_B, float lambda_B);
+
+/* Wait for the stream, at most timeout_ms milliseconds (< 0: no limit).
+ * Returns SFT_ETIMEOUT if work is still running, SFT_EINVAL if a kernel
+ * flagged bad data (the flag is then cleared), SFT_ECUDA on a CUDA error. */
+sft_status sft_sync(sft_ctx *ctx, int64_t timeout_ms);
+
+/* Change the stream later calls enqueue on. */
+sft_status sft_set_stream(sft_ctx *ctx, void *stream);
+
+/* Human-readable message of the last failure on this context ("" if none).
+ * Valid until the next call on the context. */
+const char *sft_last_error(const sft_ctx *ctx);
+
+/* Number of kernels this context has launched so far. */
+int64_t sft_launch_count(const sft_ctx *ctx);
+
+/* Free the context (host memory only).  Does not synchronise. */
+void sft_destroy(sft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFT_H */

@@ -1,0 +1,417 @@
+// sft_api.cu -- host side of the C ABI declared in include/sft.h: argument
+// validation, workspace carving and the launch sequence of each call.
+// Nothing here computes on the host; every step of the method is a kernel.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "sft_internal.cuh"
+
+using namespace sft;
+
+struct sft_ctx {
+    int N = 0;
+    int R = 0;
+    int deterministic = 0;
+    int64_t dims[kMaxOrder] = {};
+    int32_t J[kMaxOrder] = {};
+    float *A[kMaxOrder] = {};
+    float *B[kMaxOrder] = {};
+    float *C[kMaxOrder] = {};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sms = 1;
+    // workspace pieces
+    int *err = nullptr;
+    double *loss_out = nullptr;
+    double *loss_partials = nullptr;
+    int loss_max_blocks = 0;
+    float *core_partials = nullptr;
+    int core_max_blocks = 0;
+    DetFactorWs det{};
+    int64_t det_max_chunks = 0;
+    int jmax = 0;
+    int64_t launches = 0;
+    std::string last_error;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool supported_rank(int v) { return v == 4 || v == 8 || v == 16 || v == 32; }
+
+int device_sms(int *device_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (device_out) *device_out = dev;
+    return sms;
+}
+
+// Fixed part of the workspace: error flag, loss output and partials, core
+// partials.  Followed by the deterministic-factor chunk arrays.
+struct Layout {
+    size_t err, loss_out, loss_partials, core_partials, det;
+    size_t fixed_bytes;
+    size_t per_chunk_bytes;
+};
+
+Layout make_layout(int sms, int jmax, int R) {
+    Layout L{};
+    size_t off = 0;
+    L.err = off;
+    off = align_up(off + sizeof(int));
+    L.loss_out = off;
+    off = align_up(off + 2 * sizeof(double));
+    L.loss_partials = off;
+    off = align_up(off + (size_t)sms * 8 * 2 * sizeof(double));
+    L.core_partials = off;
+    off = align_up(off + (size_t)sms * 4 * jmax * R * sizeof(float));
+    L.det = off;
+    L.fixed_bytes = off;
+    L.per_chunk_bytes = (size_t)kDetChunk * sizeof(int32_t)          // part_row
+                        + (size_t)kDetChunk * jmax * sizeof(float)   // part_sum
+                        + sizeof(int32_t);                           // seg_count
+    return L;
+}
+
+const char *check_config(const sft_config *cfg, sft_status *st) {
+    *st = SFT_EINVAL;
+    if (!cfg) return "config is NULL";
+    if (cfg->order < 2 || cfg->order > kMaxOrder) return "order must be in [2, 16]";
+    if (!cfg->dims || !cfg->J) return "dims / J arrays are NULL";
+    if (cfg->R < 1) return "R must be positive";
+    for (int n = 0; n < cfg->order; ++n) {
+        if (cfg->dims[n] < 1 || cfg->dims[n] > 0x7fffffffLL) return "each I_n must be in [1, 2^31)";
+        if (cfg->J[n] < 1) return "each J_n must be positive";
+    }
+    if (cfg->prec != SFT_FP32 && cfg->prec != SFT_BF16) return "unknown precision";
+    *st = SFT_ENOTSUP;
+    if (cfg->prec != SFT_FP32) return "only SFT_FP32 is supported by this build";
+    if (!supported_rank(cfg->R)) return "R must be one of 4, 8, 16, 32";
+    for (int n = 0; n < cfg->order; ++n) {
+        if (!supported_rank(cfg->J[n])) return "each J_n must be one of 4, 8, 16, 32";
+        if (4 * cfg->J[n] < cfg->R) return "4 * J_n must be >= R";
+    }
+    *st = SFT_OK;
+    return nullptr;
+}
+
+sft_status fail(sft_ctx *c, sft_status st, const std::string &msg) {
+    if (c) c->last_error = msg;
+    return st;
+}
+
+sft_status cuda_fail(sft_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, SFT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Common validation of a pass over a COO set.
+sft_status check_set(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz) {
+    if (!idx) return fail(c, SFT_EINVAL, "idx array is NULL");
+    for (int k = 0; k < c->N; ++k)
+        if (!idx[k] && nnz > 0) return fail(c, SFT_EINVAL, "idx[k] is NULL");
+    if (!val && nnz > 0) return fail(c, SFT_EINVAL, "val is NULL");
+    if (nnz < 0 || nnz > 0x7fffffffLL) return fail(c, SFT_EINVAL, "nnz must be in [0, 2^31)");
+    return SFT_OK;
+}
+
+PassArgs pass_args(const sft_ctx *c, int mode, const int32_t *const *idx, const float *val,
+                   const uint32_t *perm, int64_t nnz, float lr, float lam) {
+    PassArgs a{};
+    for (int k = 0; k < c->N; ++k) {
+        a.idx[k] = idx[k];
+        a.C[k] = c->C[k];
+        a.dims[k] = (int32_t)c->dims[k];
+    }
+    a.N = c->N;
+    a.n = mode;
+    a.val = val;
+    a.perm = perm;
+    a.nnz = nnz;
+    a.base = 0;
+    a.count = nnz;
+    if (mode >= 0) {
+        a.A = c->A[mode];
+        a.B = c->B[mode];
+    }
+    a.lr = lr;
+    a.lam = lam;
+    a.err = c->err;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sft_workspace_bytes(const sft_config *cfg, int64_t max_batch) {
+    sft_status st;
+    if (check_config(cfg, &st)) return 0;
+    int sms = device_sms(nullptr);
+    if (sms < 1) return 0;
+    int jmax = 0;
+    for (int n = 0; n < cfg->order; ++n) jmax = cfg->J[n] > jmax ? cfg->J[n] : jmax;
+    Layout L = make_layout(sms, jmax, cfg->R);
+    int64_t b = max_batch < 1 ? 1 : (max_batch > kDetMaxBatch ? kDetMaxBatch : max_batch);
+    int64_t chunks = (b + kDetChunk - 1) / kDetChunk;
+    return L.fixed_bytes + (size_t)chunks * L.per_chunk_bytes + kAlign;
+}
+
+sft_status sft_init(const sft_config *cfg, float *const *A, float *const *B, void *const *C,
+                    void *const *A_lo, void *workspace, size_t workspace_bytes, sft_ctx **out) {
+    if (!out) return SFT_EINVAL;
+    *out = nullptr;
+    sft_status st;
+    if (check_config(cfg, &st)) return st;
+    if (!A || !B || !C) return SFT_EINVAL;
+    if (A_lo) return SFT_EINVAL;
+    for (int n = 0; n < cfg->order; ++n) {
+        if (!A[n] || !B[n] || !C[n]) return SFT_EINVAL;
+        if (!aligned16(A[n]) || !aligned16(B[n]) || !aligned16(C[n])) return SFT_EINVAL;
+    }
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0) return SFT_EINVAL;
+    int device = 0;
+    int sms = device_sms(&device);
+    if (sms < 1) return SFT_ECUDA;
+    sft_ctx *c = new (std::nothrow) sft_ctx;
+    if (!c) return SFT_ENOMEM;
+    c->N = cfg->order;
+    c->R = cfg->R;
+    c->deterministic = cfg->deterministic ? 1 : 0;
+    c->stream = (cudaStream_t)cfg->stream;
+    c->device = device;
+    c->sms = sms;
+    for (int n = 0; n < c->N; ++n) {
+        c->dims[n] = cfg->dims[n];
+        c->J[n] = cfg->J[n];
+        c->A[n] = A[n];
+        c->B[n] = B[n];
+        c->C[n] = (float *)C[n];
+        c->jmax = c->J[n] > c->jmax ? c->J[n] : c->jmax;
+    }
+    Layout L = make_layout(sms, c->jmax, c->R);
+    if (workspace_bytes < L.fixed_bytes + L.per_chunk_bytes) {
+        delete c;
+        return SFT_ENOMEM;
+    }
+    char *ws = (char *)workspace;
+    c->err = (int *)(ws + L.err);
+    c->loss_out = (double *)(ws + L.loss_out);
+    c->loss_partials = (double *)(ws + L.loss_partials);
+    c->loss_max_blocks = sms * 8;
+    c->core_partials = (float *)(ws + L.core_partials);
+    c->core_max_blocks = sms * 4;
+    c->det_max_chunks = (int64_t)((workspace_bytes - L.fixed_bytes) / L.per_chunk_bytes);
+    if (c->det_max_chunks * kDetChunk > kDetMaxBatch) c->det_max_chunks = kDetMaxBatch / kDetChunk;
+    char *d = ws + L.det;
+    c->det.part_row = (int32_t *)d;
+    d += (size_t)c->det_max_chunks * kDetChunk * sizeof(int32_t);
+    c->det.part_sum = (float *)d;
+    d += (size_t)c->det_max_chunks * kDetChunk * c->jmax * sizeof(float);
+    c->det.seg_count = (int32_t *)d;
+    cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return SFT_ECUDA;
+    }
+    *out = c;
+    return SFT_OK;
+}
+
+sft_status sft_refresh_C(sft_ctx *c, int32_t mode) {
+    if (!c) return SFT_EINVAL;
+    if (mode < -1 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    for (int n = 0; n < c->N; ++n) {
+        if (mode >= 0 && n != mode) continue;
+        cudaError_t e = launch_refresh(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R,
+                                       c->stream, c->sms);
+        c->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(c, e, "refresh launch");
+    }
+    return SFT_OK;
+}
+
+sft_status sft_update_factors(sft_ctx *c, int32_t mode, const int32_t *const *idx,
+                              const float *val, const uint32_t *perm, int64_t nnz, int64_t batch,
+                              float lr, float lambda) {
+    if (!c) return SFT_EINVAL;
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    sft_status st = check_set(c, idx, val, nnz);
+    if (st != SFT_OK) return st;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (nnz == 0) return SFT_OK;
+    PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
+    if (!c->deterministic) {
+        cudaError_t e = launch_factor_hogwild(a, c->J[mode], c->R, c->stream, c->sms);
+        c->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(c, e, "factor launch");
+        return SFT_OK;
+    }
+    if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
+    if (batch > c->det_max_chunks * kDetChunk)
+        return fail(c, SFT_ENOTSUP, "deterministic factor batch larger than the workspace allows "
+                                    "(at most 16384 and the max_batch given to sft_workspace_bytes)");
+    for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
+        a.base = b0;
+        a.count = nnz - b0 < batch ? nnz - b0 : batch;
+        cudaError_t e = launch_factor_det(a, c->J[mode], c->R, c->det, c->stream);
+        c->launches += 2;
+        if (e != cudaSuccess) return cuda_fail(c, e, "deterministic factor launch");
+    }
+    return SFT_OK;
+}
+
+sft_status sft_update_core(sft_ctx *c, int32_t mode, const int32_t *const *idx, const float *val,
+                           const uint32_t *perm, int64_t nnz, int64_t batch, float lr,
+                           float lambda) {
+    if (!c) return SFT_EINVAL;
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    sft_status st = check_set(c, idx, val, nnz);
+    if (st != SFT_OK) return st;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
+    if (nnz == 0) return SFT_OK;
+    PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
+    for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
+        a.base = b0;
+        a.count = nnz - b0 < batch ? nnz - b0 : batch;
+        int nblk = core_blocks_for(a.count, c->sms);
+        if (nblk > c->core_max_blocks) nblk = c->core_max_blocks;
+        cudaError_t e = launch_core(a, c->J[mode], c->R, c->core_partials, nblk, c->stream);
+        c->launches += 2;
+        if (e != cudaSuccess) return cuda_fail(c, e, "core launch");
+    }
+    return SFT_OK;
+}
+
+static sft_status loss_enqueue(sft_ctx *c, const int32_t *const *idx, const float *val,
+                               int64_t nnz, double *out2) {
+    sft_status st = check_set(c, idx, val, nnz);
+    if (st != SFT_OK) return st;
+    PassArgs a = pass_args(c, -1, idx, val, nullptr, nnz, 0.f, 0.f);
+    int nblk = loss_blocks_for(nnz, c->sms);
+    if (nblk > c->loss_max_blocks) nblk = c->loss_max_blocks;
+    cudaError_t e = launch_loss(a, c->R, c->loss_partials, nblk, out2, c->stream);
+    c->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(c, e, "loss launch");
+    return SFT_OK;
+}
+
+static sft_status read_flag(sft_ctx *c) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the error flag");
+    if (flag) {
+        cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        std::string m = "a kernel skipped bad data:";
+        if (flag & kErrIndex) m += " coordinate out of range;";
+        if (flag & kErrPerm) m += " permutation entry >= nnz;";
+        return fail(c, SFT_EINVAL, m);
+    }
+    return SFT_OK;
+}
+
+sft_status sft_loss(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz,
+                    double *sse, double *sae) {
+    if (!c) return SFT_EINVAL;
+    if (!sse || !sae) return fail(c, SFT_EINVAL, "sse / sae are NULL");
+    sft_status st = loss_enqueue(c, idx, val, nnz, c->loss_out);
+    if (st != SFT_OK) return st;
+    double h[2] = {0.0, 0.0};
+    cudaError_t e = cudaMemcpyAsync(h, c->loss_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "loss readback");
+    st = read_flag(c);
+    if (st != SFT_OK) return st;
+    *sse = h[0];
+    *sae = h[1];
+    return SFT_OK;
+}
+
+sft_status sft_loss_async(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz,
+                          double *out2) {
+    if (!c) return SFT_EINVAL;
+    if (!out2) return fail(c, SFT_EINVAL, "out2 is NULL");
+    return loss_enqueue(c, idx, val, nnz, out2);
+}
+
+sft_status sft_predict(sft_ctx *c, const int32_t *const *idx, int64_t nnz, float *out) {
+    if (!c) return SFT_EINVAL;
+    if (!idx) return fail(c, SFT_EINVAL, "idx array is NULL");
+    for (int k = 0; k < c->N; ++k)
+        if (!idx[k] && nnz > 0) return fail(c, SFT_EINVAL, "idx[k] is NULL");
+    if (!out && nnz > 0) return fail(c, SFT_EINVAL, "out is NULL");
+    if (nnz < 0 || nnz > 0x7fffffffLL) return fail(c, SFT_EINVAL, "nnz must be in [0, 2^31)");
+    if (nnz == 0) return SFT_OK;
+    PassArgs a = pass_args(c, -1, idx, nullptr, nullptr, nnz, 0.f, 0.f);
+    cudaError_t e = launch_predict(a, c->R, out, c->stream, c->sms);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "predict launch");
+    return SFT_OK;
+}
+
+sft_status sft_epoch(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz,
+                     const uint32_t *const *perm_factor, const uint32_t *const *perm_core,
+                     int64_t batch_factor, int64_t batch_core, float lr_A, float lambda_A,
+                     float lr_B, float lambda_B) {
+    if (!c) return SFT_EINVAL;
+    for (int n = 0; n < c->N; ++n) {
+        sft_status st = sft_update_factors(c, n, idx, val, perm_factor ? perm_factor[n] : nullptr,
+                                           nnz, batch_factor, lr_A, lambda_A);
+        if (st != SFT_OK) return st;
+        st = sft_refresh_C(c, n);
+        if (st != SFT_OK) return st;
+    }
+    for (int n = 0; n < c->N; ++n) {
+        sft_status st = sft_update_core(c, n, idx, val, perm_core ? perm_core[n] : nullptr, nnz,
+                                        batch_core, lr_B, lambda_B);
+        if (st != SFT_OK) return st;
+        st = sft_refresh_C(c, n);
+        if (st != SFT_OK) return st;
+    }
+    return SFT_OK;
+}
+
+sft_status sft_sync(sft_ctx *c, int64_t timeout_ms) {
+    if (!c) return SFT_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "stream query");
+        if (timeout_ms >= 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (ms > timeout_ms) return fail(c, SFT_ETIMEOUT, "stream still busy at the timeout");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return read_flag(c);
+}
+
+sft_status sft_set_stream(sft_ctx *c, void *stream) {
+    if (!c) return SFT_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return SFT_OK;
+}
+
+const char *sft_last_error(const sft_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+int64_t sft_launch_count(const sft_ctx *c) { return c ? c->launches : 0; }
+
+void sft_destroy(sft_ctx *c) { delete c; }
+
+}  // extern "C"

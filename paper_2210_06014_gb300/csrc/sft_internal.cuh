@@ -1,0 +1,142 @@
+// sft_internal.cuh -- kernel argument blocks, launch entry points and small
+// device helpers shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sft.h"
+
+namespace sft {
+
+constexpr int kMaxOrder = SFT_MAX_ORDER;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Error flag bits raised by kernels (device int in the workspace).
+constexpr int kErrIndex = 1;  // coordinate out of range
+constexpr int kErrPerm = 2;   // permutation entry >= nnz
+
+// Operands of one pass over the nonzeros of mode n.
+struct PassArgs {
+    const int32_t *idx[kMaxOrder];  // idx[k][s]
+    const float *C[kMaxOrder];      // cached products C^(k), I_k x R
+    int32_t dims[kMaxOrder];        // I_k
+    int N;                          // order
+    int n;                          // mode being updated
+    const float *val;               // x_s
+    const uint32_t *perm;           // visit order (NULL = storage order)
+    int64_t nnz;                    // samples in the whole pass (perm length)
+    int64_t base;                   // first visit position of this launch
+    int64_t count;                  // visit positions handled by this launch
+    float *A;                       // A^(n), I_n x J_n
+    float *B;                       // B^(n), J_n x R
+    float lr, lam;
+    int *err;                       // device error flag
+};
+
+// Workspace pieces used by the deterministic factor path.
+struct DetFactorWs {
+    int32_t *part_row;   // [chunks][kDetChunk]
+    float *part_sum;     // [chunks][kDetChunk][J]
+    int32_t *seg_count;  // [chunks]
+};
+
+constexpr int kDetChunk = 256;           // samples per CTA in the deterministic factor path
+constexpr int64_t kDetMaxBatch = 16384;  // largest deterministic factor minibatch
+
+// ----------------------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() after enqueuing.  J and R are validated by
+// the caller (sft_api.cu) against the supported set.
+cudaError_t launch_refresh(const float *A, const float *B, float *C, int64_t I, int J, int R,
+                           cudaStream_t st, int sms);
+cudaError_t launch_factor_hogwild(const PassArgs &a, int J, int R, cudaStream_t st, int sms);
+cudaError_t launch_factor_det(const PassArgs &a, int J, int R, const DetFactorWs &ws,
+                              cudaStream_t st);
+cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nblk,
+                        cudaStream_t st);
+int core_blocks_for(int64_t count, int sms);
+cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, double *out2,
+                        cudaStream_t st);
+int loss_blocks_for(int64_t count, int sms);
+cudaError_t launch_predict(const PassArgs &a, int R, float *out, cudaStream_t st, int sms);
+
+// ----------------------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ float4 ldg4(const float *p) {
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+__device__ __forceinline__ void mul4(float4 &a, const float4 &b) {
+    a.x *= b.x; a.y *= b.y; a.z *= b.z; a.w *= b.w;
+}
+
+// Visit position -> storage index, with the permutation bound check.
+__device__ __forceinline__ bool sample_at(const PassArgs &a, int64_t pos, int64_t &s) {
+    if (a.perm) {
+        uint32_t q = __ldg(a.perm + pos);
+        if ((int64_t)q >= a.nnz) {
+            atomicOr(a.err, kErrPerm);
+            return false;
+        }
+        s = q;
+    } else {
+        s = pos;
+    }
+    return true;
+}
+
+// Load a run of L consecutive floats (L in {1,2,4,8,...}) from a 4L-byte
+// aligned address into registers.
+template <int L>
+__device__ __forceinline__ void load_run(const float *p, float (&r)[L]) {
+    if constexpr (L >= 4) {
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q) {
+            float4 v = ld4(p + 4 * q);
+            r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+        }
+    } else if constexpr (L == 2) {
+        float2 v = *reinterpret_cast<const float2 *>(p);
+        r[0] = v.x; r[1] = v.y;
+    } else {
+        r[0] = *p;
+    }
+}
+
+// Sum over the T lanes of an aligned lane group (T a power of two <= 32).
+template <int T>
+__device__ __forceinline__ float group_sum(float x) {
+#pragma unroll
+    for (int w = T / 2; w >= 1; w >>= 1) x += __shfl_xor_sync(kFull, x, w);
+    return x;
+}
+
+// Reduce-scatter over the T lanes of a group: on entry every lane holds a
+// partial vector v[0..L); on exit lane `sub` holds, in v[0..L/T), the full sum
+// of elements [sub*L/T, (sub+1)*L/T).
+template <int T, int L>
+__device__ __forceinline__ void group_reduce_scatter(float (&v)[L], int sub) {
+#pragma unroll
+    for (int w = T / 2; w >= 1; w >>= 1) {
+        const int len = (L / T) * 2 * w;  // current range length
+        const bool upper = (sub & w) != 0;
+#pragma unroll
+        for (int q = 0; q < L / 2; ++q) {
+            if (q < len / 2) {
+                float send = upper ? v[q] : v[q + len / 2];
+                float keep = upper ? v[q + len / 2] : v[q];
+                float recv = __shfl_xor_sync(kFull, send, w);
+                v[q] = keep + recv;
+            }
+        }
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace sft

@@ -1,0 +1,100 @@
+"""Shared pieces of the GPU parity tests: seeded workloads, the two sides
+(libsft on the GPU, the FP64 oracle on the CPU) and the error bounds.
+
+Bounds are condition-aware: a float32 result r of a sum of products is
+compared with the float64 oracle value through |r - r_ref| <= tol * S, where S
+is the same sum taken over absolute values (the quantity that bounds the
+rounding error of any summation order).  tol is 1e-5 for float32.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+import torch
+
+TOL32 = 1e-5
+
+
+@functools.lru_cache(maxsize=None)
+def small_tensor():
+    """Order-3 1000x800x600, 200k nonzeros, planted J=R=8 (seed 0), CPU tensors."""
+    from paper_2210_06014_gb300 import synth
+    return synth.make_tensor(synth.spec_small())
+
+
+def to_dev(T):
+    idx = [i.cuda() for i in T.idx]
+    val = T.val.cuda()
+    return idx, val
+
+
+def np_idx(idx):
+    return [i.cpu().numpy().astype(np.int64) for i in idx]
+
+
+def abs_C(A, B):
+    return [np.abs(a) @ np.abs(b) for a, b in zip(A, B)]
+
+
+def pred_scale(absC, idx):
+    """sum_r prod_k |C|^(k)[i_k][r] per nonzero."""
+    prod = None
+    for k, ix in enumerate(idx):
+        rows = absC[k][ix]
+        prod = rows if prod is None else prod * rows
+    return prod.sum(axis=1)
+
+
+def factor_step_scale(A, B, n, idx, val, sel, lr, lam):
+    """Per-row bound of one minibatch factor step over samples `sel`:
+    lr * sum_s [(|x_s| + |a| . |v|_s) |v|_s + lam |a|], with |v|_s = |B^(n)| |p|_s."""
+    absC = abs_C(A, B)
+    p_abs = None
+    for k in range(len(idx)):
+        if k == n:
+            continue
+        rows = absC[k][idx[k][sel]]
+        p_abs = rows if p_abs is None else p_abs * rows
+    v_abs = p_abs @ np.abs(B[n]).T                    # M x J
+    a_abs = np.abs(A[n][idx[n][sel]])                 # M x J
+    xh_abs = np.sum(a_abs * v_abs, axis=1)
+    term = (np.abs(val[sel].astype(np.float64)) + xh_abs)[:, None] * v_abs + lam * a_abs
+    out = np.zeros_like(A[n])
+    np.add.at(out, idx[n][sel], lr * term)
+    return out
+
+
+def core_step_scale(A, B, n, idx, val, sel, lr, lam):
+    """Bound of one minibatch core step: lr * (sum_s |e|_s |a|_s |p|_s^T / M + lam |B|)."""
+    absC = abs_C(A, B)
+    p_abs = None
+    for k in range(len(idx)):
+        if k == n:
+            continue
+        rows = absC[k][idx[k][sel]]
+        p_abs = rows if p_abs is None else p_abs * rows
+    a_abs = np.abs(A[n][idx[n][sel]])
+    xh_abs = np.sum(a_abs * (p_abs @ np.abs(B[n]).T), axis=1)
+    e_abs = np.abs(val[sel].astype(np.float64)) + xh_abs
+    G = (a_abs * e_abs[:, None]).T @ p_abs
+    return lr * (G / len(sel) + lam * np.abs(B[n]))
+
+
+def assert_within(got, want, scale, tol=TOL32, what=""):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    err = np.abs(got - want)
+    bound = tol * np.asarray(scale, dtype=np.float64) + 1e-30
+    bad = err > bound
+    if bad.any():
+        i = np.unravel_index(np.argmax(err / bound), err.shape)
+        raise AssertionError(f"{what}: {bad.sum()} of {bad.size} entries beyond tol*scale; worst at "
+                             f"{i}: got {got[i]!r} want {want[i]!r} scale {np.asarray(scale)[i]!r} "
+                             f"(err/bound {float(err[i] / bound[i]):.3g})")
+
+
+def rel_fro(got, want):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    return float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300))
