@@ -3,13 +3,18 @@
 One step = one epoch of Algorithm 2 over a Netflix-shaped synthetic ratings
 tensor (480000 x 17800 x 2200, 100M nonzeros, Zipf(1.1) user / item modes,
 integer values 1-5, J = R = 16, float32; 90M train / 10M test):
-  for every mode: factor pass (Hogwild rows, Algorithm 4) + refresh of C^(n);
+  for every mode: factor pass + refresh of C^(n);
   for every mode: core pass (gradient accumulated over the whole pass and one
   update, Algorithm 5) + refresh of C^(n);
   then the test-set residual sums (RMSE / MAE).
-value = training nonzeros / epoch time.  Inputs live in HBM (1.6 GB of COO,
-larger than L2); `e2e` repeats the step with the COO copied from pinned host
-memory inside the timed region and the loss read back.
+Default path: the nonzeros of each mode are kept in its slice layout (the CSF
+slices of Section "Tensor Storage Format", built once before timing) and the
+factor pass runs every slice element by element (Algorithm 4 order); with
+--path coo the factor pass is the Hogwild COO kernel instead.
+value = training nonzeros / epoch time.  Inputs live in HBM (several GB,
+larger than L2); `e2e` repeats the step with the step's inputs (the slice
+layouts and the test set) copied from pinned host memory inside the timed
+region and the loss read back.
 
 --impl reference times the FP64 CPU oracle on a bounded prefix of the same
 workload (the only CPU code this script runs).
@@ -46,6 +51,7 @@ def parse():
                    help="nonzeros of the oracle's bounded CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--path", default="slices", choices=["slices", "coo"])
     return p.parse_args()
 
 
@@ -156,13 +162,16 @@ def sum_over_ranks(x, world):
     return float(t.item())
 
 
-def algorithmic_bytes(N, J, R):
+def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0):
     """Bytes per nonzero of one factor / core pass (float32): the COO entry,
     the N-1 gathered C rows, and the factor row (read + write for the factor
-    pass, read for the core pass)."""
+    pass, read for the core pass).  On the slice layout a factor row is read
+    and written once per slice instead of once per nonzero, so its bytes are
+    scaled by rows_per_nnz = (touched rows) / nnz."""
     coo = 4 * N + 4
     gather = (N - 1) * R * 4
-    return coo + gather + 2 * J * 4, coo + gather + J * 4
+    f = rows_per_nnz if path == "slices" else 1.0
+    return coo + gather + 2 * J * 4 * f, coo + gather + J * 4 * f
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -238,6 +247,17 @@ def main():
     stream = torch.cuda.current_stream()
     dec = sft.Decomposition(T.A0, T.B0, deterministic=False, max_batch=4096)
     loss_out = torch.zeros(2, dtype=torch.float64, device=dev)
+    slices = []
+    layout_s = 0.0
+    rows_per_nnz = 1.0
+    if args.path == "slices":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slices = [dec.slices(n, idx, val, None) for n in range(N)]
+        torch.cuda.synchronize()
+        layout_s = time.perf_counter() - t0
+        touched = [int((sl.row_ptr[1:] > sl.row_ptr[:-1]).sum()) for sl in slices]
+        rows_per_nnz = sum(touched) / (N * nnz)
 
     ev = {}
 
@@ -248,21 +268,19 @@ def main():
         return a, b
 
     def step(timed: bool, src=None):
-        """One epoch; with src = (host idx, host val, host test idx, host test val) the
-        COO is first copied from pinned host memory."""
+        """One epoch; with src = (host copies of the step's inputs) they are first
+        copied from pinned host memory."""
         if src is not None:
-            hidx, hval, htidx, htval = src
-            for d, h in zip(idx, hidx):
+            for d, h in zip(src[0], src[1]):
                 d.copy_(h, non_blocking=True)
-            val.copy_(hval, non_blocking=True)
-            for d, h in zip(tidx, htidx):
-                d.copy_(h, non_blocking=True)
-            tval.copy_(htval, non_blocking=True)
         for n in range(N):
             if timed:
                 a, b = ev_pair("factor")
                 a.record(stream)
-            dec.update_factors(n, idx, val, None, batch=4096, lr=0.01, lam=0.01)
+            if slices:
+                dec.update_factors_slices(slices[n], lr=0.01, lam=0.01)
+            else:
+                dec.update_factors(n, idx, val, None, batch=4096, lr=0.01, lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
@@ -274,7 +292,10 @@ def main():
             if timed:
                 a, b = ev_pair("core")
                 a.record(stream)
-            dec.update_core(n, idx, val, None, batch=core_batch, lr=0.01, lam=0.01)
+            if slices:
+                dec.update_core_slices(slices[n], batch=core_batch, lr=0.01, lam=0.01)
+            else:
+                dec.update_core(n, idx, val, None, batch=core_batch, lr=0.01, lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
@@ -319,7 +340,7 @@ def main():
     c_ms, c_step = avg_ms("core", N)
     r_ms, r_step = avg_ms("refresh", 2 * N)
     l_ms, l_step = avg_ms("loss", 1)
-    fac_bytes, core_bytes = algorithmic_bytes(N, J, R)
+    fac_bytes, core_bytes = algorithmic_bytes(N, J, R, args.path, rows_per_nnz)
     peak, peak_kind = peaks()
     kernels = {
         "factor": (f_ms, fac_bytes * nnz / (f_ms / 1e3) / 1e9),
@@ -333,13 +354,14 @@ def main():
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hidx = [i.cpu().pin_memory() for i in idx]
-        hval = val.cpu().pin_memory()
-        htidx = [i.cpu().pin_memory() for i in tidx]
-        htval = tval.cpu().pin_memory()
-        src = (hidx, hval, htidx, htval)
-        h2d = sum(i.numel() * 4 for i in hidx) + hval.numel() * 4 + \
-            sum(i.numel() * 4 for i in htidx) + htval.numel() * 4
+        if slices:
+            dev_in = [t for sl in slices for t in sl.idx + [sl.val, sl.row_ptr]]
+        else:
+            dev_in = list(idx) + [val]
+        dev_in += list(tidx) + [tval]
+        host_in = [t.cpu().pin_memory() for t in dev_in]
+        src = (dev_in, host_in)
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
         hloss = torch.zeros(2, dtype=torch.float64).pin_memory()
         step(False, src)
         torch.cuda.synchronize()
@@ -369,8 +391,13 @@ def main():
             "config": {
                 "workload": workload, "train_nnz": nnz, "test_nnz": ntest, "J": J, "R": R,
                 "parallelism": "replicas only" if world > 1 else "single GPU",
-                "schedule": "factor: Hogwild rows (Algorithm 4); core: one update per pass "
-                            f"(batch {core_batch}); refresh after every pass; test loss",
+                "path": args.path,
+                "schedule": ("factor: every mode-n slice element by element (Algorithm 4 order, "
+                             "slice layout)" if slices else "factor: Hogwild rows (COO)")
+                            + f"; core: batch {core_batch} (Algorithm 5 when = nnz); refresh "
+                              "after every pass; test loss",
+                "layout_build_s": round(layout_s, 3),
+                "factor_rows_per_nnz": rows_per_nnz,
                 "l2": "inputs larger than L2 (COO 1.6 GB)", "generation_s": round(gen_s, 2),
                 "test_rmse_after": test_rmse,
                 "per_launch_ms": {"factor": f_ms, "core": c_ms, "refresh": r_ms, "loss": l_ms},

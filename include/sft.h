@@ -147,6 +147,60 @@ sft_status sft_epoch(sft_ctx *ctx, const int32_t *const *idx, const float *val, 
                      int64_t batch_factor, int64_t batch_core, float lr_A, float lambda_A,
                      float lr_B, float lambda_B);
 
+/* ---------------------------------------------------------------------------
+ * Slice layout.  A "slice" of mode n is the set of nonzeros that share the
+ * coordinate i_n -- the first level of the CSF tree of Section "Tensor
+ * Storage Format".  The sliced copy of a COO set holds the same nonzeros
+ * ordered by (i_n, visit position): slice i occupies positions
+ * [row_ptr[i], row_ptr[i+1]) and keeps the caller's visit order inside.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device scratch sft_group_slices needs for nnz nonzeros. */
+size_t sft_slices_scratch_bytes(int64_t nnz);
+
+/* Build the slice layout of mode `mode` on the device (a bitonic sort of
+ * (i_mode, position) keys, then a gather).  out_idx: N device arrays of nnz
+ * int32; out_val: nnz float32; out_row_ptr: I_mode + 1 int32.  perm as in
+ * sft_update_factors (NULL = storage order).  Nonzeros with a coordinate out
+ * of range are moved behind the last slice and flagged (SFT_EINVAL at the next
+ * sft_sync).  Enqueues only. */
+sft_status sft_group_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *idx, const float *val,
+                            const uint32_t *perm, int64_t nnz, int32_t *const *out_idx,
+                            float *out_val, int32_t *out_row_ptr, void *scratch,
+                            size_t scratch_bytes);
+
+/* Bytes of device workspace sft_update_factors_slices needs for a slice layout
+ * of nnz nonzeros of mode `mode` under the context's current tiling. */
+size_t sft_slices_workspace_bytes(const sft_ctx *ctx, int32_t mode, int64_t nnz);
+
+/* One factor pass over A^(mode) on a slice layout, element by element
+ * (Algorithm 4; Eq. (9)-(10) with batch 1): every slice's nonzeros are run in
+ * their stored order, so the result equals the sequential pass over the visit
+ * order that built the layout (slices of one mode never interact during a
+ * factor pass).  Long slices are cut into tile-sized pieces composed as affine
+ * maps and applied in order (same recurrence, re-associated).  Deterministic,
+ * no atomics.  workspace: device buffer of sft_slices_workspace_bytes bytes.
+ * Enqueues only. */
+sft_status sft_update_factors_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
+                                     const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                     float lr, float lambda, void *workspace,
+                                     size_t workspace_bytes);
+
+/* One core pass over B^(mode) on a slice layout (Algorithm 5; Eq. (9), (11)):
+ * minibatches are consecutive ranges of `batch` positions of the layout
+ * (batch = nnz: one update per pass).  G is accumulated per slice run as
+ * a_i (sum_s e_s p_s)^T.  Deterministic.  Enqueues only. */
+sft_status sft_update_core_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
+                                  const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                  int64_t batch, float lr, float lambda);
+
+/* Tiling of the slice passes: tile = positions per work item (0 = automatic),
+ * max_direct = longest slice that crosses a tile boundary and is still run
+ * element by element by one lane group (0 = automatic, < 0 = none: every
+ * crossing slice is split into maps).  Results do not depend on it beyond
+ * rounding. */
+sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
+
 /* Wait for the stream, at most timeout_ms milliseconds (< 0: no limit).
  * Returns SFT_ETIMEOUT if work is still running, SFT_EINVAL if a kernel
  * flagged bad data (the flag is then cleared), SFT_ECUDA on a CUDA error. */

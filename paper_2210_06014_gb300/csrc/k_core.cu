@@ -170,8 +170,12 @@ cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nb
     SFT_DISPATCH_RJ(R, J, (k_core_grad<R_, J_><<<nblk, kCoreThreads, 0, st>>>(a, partials)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int JR = J * R;
-    k_core_apply<<<(JR + 255) / 256, 256, 0, st>>>(a.B, partials, nblk, JR, a.count, a.lr, a.lam);
+    return launch_core_apply(a.B, partials, nblk, J * R, a.count, a.lr, a.lam, st);
+}
+
+cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
+                              float lr, float lam, cudaStream_t st) {
+    k_core_apply<<<(JR + 255) / 256, 256, 0, st>>>(B, partials, nblk, JR, Mb, lr, lam);
     return cudaGetLastError();
 }
 

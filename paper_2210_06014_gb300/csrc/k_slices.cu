@@ -1,0 +1,728 @@
+// k_slices.cu -- the factor and core passes over nonzeros grouped into the
+// mode-n slices of the tensor (all nonzeros that share i_n, kept in visit
+// order), the CSF layout of Section "Tensor Storage Format".
+//
+// Layout.  k_slice_keys / k_bitonic_* / k_slice_gather / k_slice_rowptr sort
+// the visit positions by (i_n, position) -- a bitonic sort of unique 64-bit
+// keys, so the order inside a slice is the visit order -- and copy the COO
+// arrays into that order; row_ptr[i] is the first position of slice i.
+//
+// Factor pass (Eq. (9)-(10), element by element as in Algorithm 4).  During a
+// factor pass over mode n a nonzero reads and writes only a_{i_n}; slices are
+// independent, and running every slice's nonzeros one after another in visit
+// order reproduces the element-by-element rule exactly.  Work is cut into
+// tiles of W consecutive positions, one lane group (T = R/4 lanes) per tile:
+//   - a slice that lies inside a tile is run directly: the row stays in
+//     registers, each nonzero does e = x - a.(B p), a += lr (e v - lambda a);
+//   - a slice that crosses tile boundaries and has at most Lseq nonzeros is run
+//     directly, whole, by the group that owns its first boundary;
+//   - a longer slice is split at the tile boundaries.  One step is the affine
+//     map a -> M_t a + c_t with M_t = (1 - lr lambda) I - lr v v^T and
+//     c_t = lr x v, so each piece is composed into one map (M, c) in parallel
+//     (k_slices_maps) and k_slices_combine applies the pieces to the row in
+//     order.  This is the same recurrence, re-associated.
+// Nothing is atomic and the result is bitwise reproducible.
+//
+// Core pass (Eq. (9), (11), Algorithm 5).  With A^(n) fixed,
+//   G = sum_s e_s a_{i_n(s)} p_s^T = sum_slices a_i (sum_{s in slice} e_s p_s)^T,
+// so a group keeps q = sum e_s p_s over the run of a slice inside its tile and
+// adds a_i q^T to its shared-memory tile of G once per run.  x^_s = (B^T a).p_s
+// uses w = B^T a computed once per run.
+#include "dispatch.cuh"
+#include "sft_internal.cuh"
+
+namespace sft {
+
+// ============================================================================ layout
+constexpr int kSortBlock = 2048;
+
+__global__ void k_slice_keys(const int32_t *__restrict__ rowidx, const uint32_t *__restrict__ perm,
+                             int64_t nnz, int32_t In, unsigned long long *__restrict__ keys,
+                             int64_t P, int *err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
+        unsigned long long key = ~0ull;
+        if (i < nnz) {
+            int64_t s = i;
+            uint32_t row = (uint32_t)In;  // invalid samples sort after every slice
+            bool ok = true;
+            if (perm) {
+                const uint32_t q = perm[i];
+                if ((int64_t)q >= nnz) {
+                    atomicOr(err, kErrPerm);
+                    ok = false;
+                } else {
+                    s = q;
+                }
+            }
+            if (ok) {
+                const uint32_t r = (uint32_t)rowidx[s];
+                if (r >= (uint32_t)In) atomicOr(err, kErrIndex);
+                else row = r;
+            }
+            key = ((unsigned long long)row << 32) | (unsigned long long)i;
+        }
+        keys[i] = key;
+    }
+}
+
+// Bitonic stages with partner distance < kSortBlock, in shared memory.  For
+// k_lo == 2 it sorts every block fully (k = 2 .. kSortBlock); otherwise it
+// finishes the merge of size k_lo (== k_hi) from distance kSortBlock/2 down.
+__global__ void __launch_bounds__(kSortBlock / 2) k_bitonic_local(unsigned long long *keys,
+                                                                   int64_t k_lo, int64_t k_hi) {
+    __shared__ unsigned long long s[kSortBlock];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+    s[t] = keys[base + t];
+    s[t + kSortBlock / 2] = keys[base + t + kSortBlock / 2];
+    __syncthreads();
+    for (int64_t k = k_lo; k <= k_hi; k <<= 1) {
+        for (int j = (int)(k / 2 < kSortBlock / 2 ? k / 2 : kSortBlock / 2); j > 0; j >>= 1) {
+            const int i = 2 * j * (t / j) + (t % j);
+            const bool up = ((base + i) & k) == 0;
+            const unsigned long long x = s[i], y = s[i + j];
+            if ((x > y) == up) {
+                s[i] = y;
+                s[i + j] = x;
+            }
+            __syncthreads();
+        }
+    }
+    keys[base + t] = s[t];
+    keys[base + t + kSortBlock / 2] = s[t + kSortBlock / 2];
+}
+
+__global__ void k_bitonic_global(unsigned long long *keys, int64_t P, int64_t k, int64_t j) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P / 2; t += stride) {
+        const int64_t i = 2 * j * (t / j) + (t % j);
+        const bool up = (i & k) == 0;
+        const unsigned long long x = keys[i], y = keys[i + j];
+        if ((x > y) == up) {
+            keys[i] = y;
+            keys[i + j] = x;
+        }
+    }
+}
+
+struct SliceOut {
+    int32_t *idx[kMaxOrder];
+    float *val;
+};
+
+__global__ void k_slice_gather(PassArgs a, const unsigned long long *__restrict__ keys, SliceOut o) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.nnz; t += stride) {
+        const unsigned long long key = keys[t];
+        const uint32_t row = (uint32_t)(key >> 32);
+        const int64_t pos = (int64_t)(key & 0xffffffffu);
+        if (row >= (uint32_t)a.dims[a.n]) {
+            for (int k = 0; k < a.N; ++k) o.idx[k][t] = -1;
+            o.val[t] = 0.f;
+            continue;
+        }
+        const int64_t s = a.perm ? (int64_t)a.perm[pos] : pos;
+        for (int k = 0; k < a.N; ++k) o.idx[k][t] = a.idx[k][s];
+        o.val[t] = a.val[s];
+    }
+}
+
+__global__ void k_slice_rowptr(const unsigned long long *__restrict__ keys, int64_t nnz, int32_t In,
+                               int32_t *__restrict__ row_ptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= In; r += stride) {
+        int64_t lo = 0, hi = nnz;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(keys[mid] >> 32) < r) lo = mid + 1; else hi = mid;
+        }
+        row_ptr[r] = (int32_t)lo;
+    }
+}
+
+int64_t slice_sort_length(int64_t nnz) {
+    int64_t P = kSortBlock;
+    while (P < nnz) P <<= 1;
+    return P;
+}
+
+cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
+                                int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
+                                int sms, int64_t *launches) {
+    const int64_t P = slice_sort_length(a.nnz);
+    const int th = 256;
+    auto grid = [&](int64_t n) {
+        int64_t b = (n + th - 1) / th;
+        const int64_t cap = (int64_t)sms * 16;
+        return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+    };
+    k_slice_keys<<<grid(P), th, 0, st>>>(a.idx[a.n], a.perm, a.nnz, a.dims[a.n], keys, P, a.err);
+    k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, 2, kSortBlock);
+    *launches += 2;
+    for (int64_t k = 2 * kSortBlock; k <= P; k <<= 1) {
+        for (int64_t j = k / 2; j >= kSortBlock; j >>= 1) {
+            k_bitonic_global<<<grid(P / 2), th, 0, st>>>(keys, P, k, j);
+            *launches += 1;
+        }
+        k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, k, k);
+        *launches += 1;
+    }
+    SliceOut o{};
+    for (int k = 0; k < a.N; ++k) o.idx[k] = out_idx[k];
+    o.val = out_val;
+    k_slice_gather<<<grid(a.nnz), th, 0, st>>>(a, keys, o);
+    k_slice_rowptr<<<grid((int64_t)a.dims[a.n] + 1), th, 0, st>>>(keys, a.nnz, a.dims[a.n], row_ptr);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+// ============================================================================ shared pieces
+// NO = number of "other" mode slots (modes != n), a compile-time bound on N-1.
+template <int NO>
+struct Sample {
+    int32_t i[NO];
+    float x;
+    bool ok;
+};
+
+// Coordinates of the other modes and the value at slice-ordered position t
+// (bounds-checked; the slice's own coordinate is known from the layout).
+template <int NO>
+__device__ __forceinline__ void load_sample(const PassArgs &a, int64_t t, bool valid, Sample<NO> &c) {
+    c.ok = valid;
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+        c.i[q] = 0;
+        if (c.ok && q < a.N - 1) {
+            const int32_t v = __ldg(a.oidx[q] + t);
+            if ((uint32_t)v >= (uint32_t)a.odims[q]) {
+                atomicOr(a.err, kErrIndex);
+                c.ok = false;
+            } else {
+                c.i[q] = v;
+            }
+        }
+    }
+    c.x = c.ok ? __ldg(a.val + t) : 0.f;
+}
+
+template <int NO>
+struct Rows {
+    float4 r[NO];
+};
+
+template <int NO, int R>
+__device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c, int sub,
+                                          Rows<NO> &w) {
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+        w.r[q] = (c.ok && q < a.N - 1) ? ldg4(a.oC[q] + (int64_t)c.i[q] * R + 4 * sub)
+                                       : make_float4(1.f, 1.f, 1.f, 1.f);
+}
+
+template <int NO>
+__device__ __forceinline__ float4 product(const Rows<NO> &w) {
+    float4 p = w.r[0];
+#pragma unroll
+    for (int q = 1; q < NO; ++q) mul4(p, w.r[q]);
+    return p;
+}
+
+struct SliceArgs {
+    PassArgs a;              // idx / val in slice order, perm unused
+    const int32_t *row_ptr;  // I_n + 1 slice starts
+    int64_t W;               // tile length
+    int64_t Lseq;            // crossing slices longer than this are split into maps
+    int64_t ntiles;
+    float *maps;             // [ntiles][2][J*J + J]
+};
+
+// Slice [s, e) of row r is consistent with the layout and the position bounds.
+__device__ __forceinline__ bool slice_ok(const SliceArgs &g, int64_t s, int64_t e) {
+    return 0 <= s && s < e && e <= g.a.nnz;
+}
+
+// ============================================================================ factor: direct run
+// Runs positions [s0, s1) of slice r element by element.  The lane holds the
+// JL entries [sub*JL, (sub+1)*JL) of a_r.  The next position's coordinates and
+// cached rows are loaded while the current one is computed.
+template <int NB, int R, int J>
+__device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, int32_t r,
+                                           int64_t s0, int64_t s1, int sub, unsigned m) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    const PassArgs &a = g.a;
+    float av[JL];
+    float *arow = a.A + (int64_t)r * J + sub * JL;
+    load_run<JL>(arow, av);
+    Sample<NB> c;
+    Rows<NB> w0, w1;
+    load_sample<NB>(a, s0, true, c);
+    load_rows<NB, R>(a, c, sub, w0);
+    float x0 = c.x;
+    bool ok0 = c.ok;
+    load_sample<NB>(a, s0 + 1, s0 + 1 < s1, c);
+    for (int64_t t = s0; t < s1; ++t) {
+        load_rows<NB, R>(a, c, sub, w1);  // position t+1 (identity rows when past the end)
+        const float x1 = c.x;
+        const bool ok1 = c.ok;
+        load_sample<NB>(a, t + 2, t + 2 < s1, c);
+        const float4 p = product<NB>(w0);
+        float vp[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+            vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
+        }
+        group_reduce_scatter_m<T, J>(vp, sub, m);
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vp[q], dot);
+        const float e = x0 - group_sum_m<T>(dot, m);
+        if (ok0) {
+#pragma unroll
+            for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vp[q] - a.lam * av[q]);
+        }
+        w0 = w1;
+        x0 = x1;
+        ok0 = ok1;
+    }
+    if constexpr (JL >= 4) {
+#pragma unroll
+        for (int q = 0; q < JL / 4; ++q)
+            *reinterpret_cast<float4 *>(arow + 4 * q) =
+                make_float4(av[4 * q], av[4 * q + 1], av[4 * q + 2], av[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < JL; ++q) arow[q] = av[q];
+    }
+}
+
+// Finds the crossing slice whose first tile boundary is b (1 <= b < ntiles).
+__device__ __forceinline__ bool first_boundary_slice(const SliceArgs &g, int64_t b, int32_t &r,
+                                                     int64_t &s, int64_t &e) {
+    const int64_t q = b * g.W;
+    if (q >= g.a.nnz) return false;
+    const int32_t *rowidx = g.a.idx[g.a.n];
+    r = __ldg(rowidx + q);
+    if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n] || __ldg(rowidx + q - 1) != r) return false;
+    s = __ldg(g.row_ptr + r);
+    e = __ldg(g.row_ptr + r + 1);
+    if (!slice_ok(g, s, e) || s >= q || e <= q) {
+        atomicOr(g.a.err, kErrIndex);
+        return false;
+    }
+    return s / g.W + 1 == b;
+}
+
+constexpr int kSliceThreads = 256;
+
+// Items [0, ntiles-1): tile boundaries (whole crossing slices of at most Lseq
+// nonzeros); items [ntiles-1, 2 ntiles - 1): tiles (slices inside the tile).
+template <int NB, int R, int J>
+__global__ void __launch_bounds__(kSliceThreads) k_slices_direct(SliceArgs g) {
+    constexpr int T = R / 4;
+    __shared__ __align__(16) float sB[J * R];
+    for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const unsigned m = group_mask<T>(lane);
+    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
+    const int64_t nb = g.ntiles - 1;
+    const int32_t *rowidx = g.a.idx[g.a.n];
+    for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
+         item < nb + g.ntiles; item += groups) {
+        if (item < nb) {
+            int32_t r;
+            int64_t s, e;
+            if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
+                run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
+            continue;
+        }
+        const int64_t t = item - nb;
+        const int64_t p0 = t * g.W;
+        const int64_t p1 = min(g.a.nnz, p0 + g.W);
+        int64_t pos = p0;
+        while (pos < p1) {
+            const int32_t r = __ldg(rowidx + pos);
+            if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) {  // invalid samples sit at the end
+                ++pos;
+                continue;
+            }
+            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+            if (!slice_ok(g, s, e) || pos < s || pos >= e) {
+                atomicOr(g.a.err, kErrIndex);
+                break;
+            }
+            const int64_t se = min(e, p1);
+            if (s >= p0 && e <= p1) run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
+            pos = se;
+        }
+    }
+}
+
+// ============================================================================ factor: long slices
+// Composes the steps of positions [s0, s1) of one slice into the affine map
+// (M, c) with a_after = M a_before + c.  The lane holds rows [sub*JL, ...) of M
+// and c.
+template <int NB, int R, int J>
+__device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, int64_t s0,
+                                            int64_t s1, int sub, unsigned m, float *out) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    const PassArgs &a = g.a;
+    const float alpha = 1.f - a.lr * a.lam;
+    float M[JL][J], cv[JL];
+#pragma unroll
+    for (int q = 0; q < JL; ++q) {
+        cv[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < J; ++k) M[q][k] = (sub * JL + q == k) ? 1.f : 0.f;
+    }
+    Sample<NB> c;
+    Rows<NB> w0, w1;
+    load_sample<NB>(a, s0, true, c);
+    load_rows<NB, R>(a, c, sub, w0);
+    float x0 = c.x;
+    bool ok0 = c.ok;
+    load_sample<NB>(a, s0 + 1, s0 + 1 < s1, c);
+    for (int64_t t = s0; t < s1; ++t) {
+        load_rows<NB, R>(a, c, sub, w1);
+        const float x1 = c.x;
+        const bool ok1 = c.ok;
+        load_sample<NB>(a, t + 2, t + 2 < s1, c);
+        const float4 p = product<NB>(w0);
+        float v[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+            v[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
+        }
+        group_reduce_scatter_m<T, J>(v, sub, m);  // v[0..JL): the lane's slice of v
+        // w = v^T M (all J columns), s = v . c
+        float w[J];
+#pragma unroll
+        for (int k = 0; k < J; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < JL; ++q) acc = fmaf(v[q], M[q][k], acc);
+            w[k] = acc;
+        }
+        float sc = 0.f;
+#pragma unroll
+        for (int q = 0; q < JL; ++q) sc = fmaf(v[q], cv[q], sc);
+#pragma unroll
+        for (int k = 0; k < J; ++k) w[k] = group_sum_m<T>(w[k], m);
+        sc = group_sum_m<T>(sc, m);
+        if (ok0) {
+#pragma unroll
+            for (int q = 0; q < JL; ++q) {
+                const float lv = a.lr * v[q];
+#pragma unroll
+                for (int k = 0; k < J; ++k) M[q][k] = fmaf(alpha, M[q][k], -lv * w[k]);
+                cv[q] = fmaf(alpha, cv[q], lv * (x0 - sc));
+            }
+        }
+        w0 = w1;
+        x0 = x1;
+        ok0 = ok1;
+    }
+#pragma unroll
+    for (int q = 0; q < JL; ++q) {
+#pragma unroll
+        for (int k = 0; k < J; ++k) out[(sub * JL + q) * J + k] = M[q][k];
+        out[J * J + sub * JL + q] = cv[q];
+    }
+}
+
+// One group per tile: maps for the tile's first run (if its slice started
+// before the tile) and last run (if its slice continues after the tile) when
+// that slice is longer than Lseq.
+template <int NB, int R, int J>
+__global__ void __launch_bounds__(kSliceThreads) k_slices_maps(SliceArgs g) {
+    constexpr int T = R / 4;
+    __shared__ __align__(16) float sB[J * R];
+    for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const unsigned m = group_mask<T>(lane);
+    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
+    const int32_t *rowidx = g.a.idx[g.a.n];
+    for (int64_t t = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T; t < g.ntiles;
+         t += groups) {
+        const int64_t p0 = t * g.W;
+        const int64_t p1 = min(g.a.nnz, p0 + g.W);
+        for (int side = 0; side < 2; ++side) {
+            const int64_t at = side == 0 ? p0 : p1 - 1;
+            const int32_t r = __ldg(rowidx + at);
+            if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) continue;
+            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+            if (!slice_ok(g, s, e) || at < s || at >= e) {
+                atomicOr(g.a.err, kErrIndex);
+                continue;
+            }
+            if (e - s <= g.Lseq) continue;
+            const bool before = s < p0, after = e > p1;
+            // slot 0: run that started before the tile; slot 1: run that starts in
+            // the tile and continues after it
+            if (side == 0 && before) {
+                compose_map<NB, R, J>(g, sB, p0, min(e, p1), sub, m,
+                                      g.maps + (t * 2 + 0) * (int64_t)(J * J + J));
+            } else if (side == 1 && after && !before) {
+                compose_map<NB, R, J>(g, sB, max(s, p0), p1, sub, m,
+                                      g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
+            } else if (side == 1 && after && before && s >= p0) {
+                // unreachable: a run that starts before the tile is handled by side 0
+            }
+        }
+    }
+}
+
+// One group per long crossing slice: applies its maps in tile order.
+template <int R, int J>
+__global__ void __launch_bounds__(kSliceThreads) k_slices_combine(SliceArgs g) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int MS = J * J + J;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const unsigned m = group_mask<T>(lane);
+    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
+    for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
+         item < g.ntiles - 1; item += groups) {
+        int32_t r;
+        int64_t s, e;
+        if (!first_boundary_slice(g, item + 1, r, s, e) || e - s <= g.Lseq) continue;
+        float *arow = g.a.A + (int64_t)r * J + sub * JL;
+        float av[JL];
+        load_run<JL>(arow, av);
+        const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
+        for (int64_t t = t0; t <= t1; ++t) {
+            const int slot = s < t * g.W ? 0 : 1;
+            const float *mp = g.maps + (t * 2 + slot) * (int64_t)MS;
+            float full[J];
+#pragma unroll
+            for (int k = 0; k < J; ++k) full[k] = __shfl_sync(m, av[k % JL], k / JL, T);
+#pragma unroll
+            for (int q = 0; q < JL; ++q) {
+                const float *row = mp + (sub * JL + q) * J;
+                float acc = __ldcg(mp + J * J + sub * JL + q);
+#pragma unroll
+                for (int k = 0; k < J; ++k) acc = fmaf(__ldcg(row + k), full[k], acc);
+                av[q] = acc;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < JL; ++q) arow[q] = av[q];
+    }
+}
+
+// ============================================================================ core
+// Dynamic shared memory: B (J*R) then one G tile (J*R) per lane group.
+constexpr int kCoreSliceThreads = 128;
+
+template <int NB, int R, int J>
+__global__ void __launch_bounds__(kCoreSliceThreads) k_slices_core(SliceArgs g,
+                                                                   float *__restrict__ partials) {
+    constexpr int T = R / 4;
+    constexpr int GPB = kCoreSliceThreads / T;
+    constexpr int JR = J * R;
+    extern __shared__ __align__(16) float smem[];
+    float *sB = smem;
+    float *sG = smem + JR;
+    for (int q = threadIdx.x; q < JR; q += blockDim.x) sB[q] = g.a.B[q];
+    for (int q = threadIdx.x; q < GPB * JR; q += blockDim.x) sG[q] = 0.f;
+    __syncthreads();
+    const PassArgs &a = g.a;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const int gid = threadIdx.x / T;
+    const unsigned m = group_mask<T>(lane);
+    float *myG = sG + gid * JR;
+    const int64_t lo = a.base, hi = a.base + a.count;  // minibatch range of positions
+    const int64_t ntiles = (a.count + g.W - 1) / g.W;
+    const int64_t groups = (int64_t)gridDim.x * GPB;
+    const int32_t *rowidx = a.idx[a.n];
+    for (int64_t t = (int64_t)blockIdx.x * GPB + gid; t < ntiles; t += groups) {
+        const int64_t p0 = lo + t * g.W;
+        const int64_t p1 = min(hi, p0 + g.W);
+        int64_t pos = p0;
+        while (pos < p1) {
+            const int32_t r = __ldg(rowidx + pos);
+            if ((uint32_t)r >= (uint32_t)a.dims[a.n]) {
+                ++pos;
+                continue;
+            }
+            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+            if (!slice_ok(g, s, e) || pos < s || pos >= e) {
+                atomicOr(a.err, kErrIndex);
+                break;
+            }
+            const int64_t se = min(e, p1);
+            // the whole a row (same addresses across the group) and w = B^T a (lane's 4 r)
+            float arow[J];
+            load_run<J>(a.A + (int64_t)r * J, arow);
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+                w.x = fmaf(arow[j], b.x, w.x);
+                w.y = fmaf(arow[j], b.y, w.y);
+                w.z = fmaf(arow[j], b.z, w.z);
+                w.w = fmaf(arow[j], b.w, w.w);
+            }
+            float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+            Sample<NB> c;
+            Rows<NB> w0, w1;
+            load_sample<NB>(a, pos, true, c);
+            load_rows<NB, R>(a, c, sub, w0);
+            float x0 = c.x;
+            bool ok0 = c.ok;
+            load_sample<NB>(a, pos + 1, pos + 1 < se, c);
+            for (int64_t u = pos; u < se; ++u) {
+                load_rows<NB, R>(a, c, sub, w1);
+                const float x1 = c.x;
+                const bool ok1 = c.ok;
+                load_sample<NB>(a, u + 2, u + 2 < se, c);
+                const float4 p = product<NB>(w0);
+                const float part = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, w.w * p.w)));
+                const float xh = group_sum_m<T>(part, m);
+                const float ev = ok0 ? x0 - xh : 0.f;
+                qv.x = fmaf(ev, p.x, qv.x);
+                qv.y = fmaf(ev, p.y, qv.y);
+                qv.z = fmaf(ev, p.z, qv.z);
+                qv.w = fmaf(ev, p.w, qv.w);
+                w0 = w1;
+                x0 = x1;
+                ok0 = ok1;
+            }
+            // G[j][4 sub .. 4 sub + 3] += a_j q  (the lane's four columns of the group tile)
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                float4 *gp = reinterpret_cast<float4 *>(&myG[j * R + 4 * sub]);
+                float4 v = *gp;
+                v.x = fmaf(arow[j], qv.x, v.x);
+                v.y = fmaf(arow[j], qv.y, v.y);
+                v.z = fmaf(arow[j], qv.z, v.z);
+                v.w = fmaf(arow[j], qv.w, v.w);
+                *gp = v;
+            }
+            pos = se;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < JR; q += blockDim.x) {
+        float acc = 0.f;
+        for (int k = 0; k < GPB; ++k) acc += sG[k * JR + q];
+        partials[(int64_t)blockIdx.x * JR + q] = acc;
+    }
+}
+
+// ============================================================================ launchers
+int slice_tile_length(int64_t nnz, int sms) {
+    int64_t W = nnz / ((int64_t)sms * 2048);
+    if (W < 32) W = 32;
+    if (W > 2048) W = 2048;
+    return (int)W;
+}
+
+template <typename K>
+static int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block, int64_t items,
+                    int sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t b = (items + items_per_block - 1) / items_per_block;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int NB, int R, int J>
+static void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st, int sms,
+                            int64_t *launches) {
+    const int gpb = kSliceThreads / (R / 4);
+    const int gd = grid_for(k_slices_direct<NB, R, J>, kSliceThreads, 0, gpb, 2 * g.ntiles - 1, sms);
+    k_slices_direct<NB, R, J><<<gd, kSliceThreads, 0, st>>>(g);
+    *launches += 1;
+    if (with_maps && g.ntiles > 1) {
+        const int gm = grid_for(k_slices_maps<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
+        k_slices_maps<NB, R, J><<<gm, kSliceThreads, 0, st>>>(g);
+        const int gc = grid_for(k_slices_combine<R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
+        k_slices_combine<R, J><<<gc, kSliceThreads, 0, st>>>(g);
+        *launches += 2;
+    }
+}
+
+template <int NB, int R, int J>
+static int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStream_t st,
+                         int sms) {
+    constexpr int T = R / 4;
+    const size_t smem = (size_t)(1 + kCoreSliceThreads / T) * J * R * sizeof(float);
+    cudaFuncSetAttribute(k_slices_core<NB, R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int nblk = grid_for(k_slices_core<NB, R, J>, kCoreSliceThreads, smem, kCoreSliceThreads / T,
+                        g.ntiles, sms);
+    if (nblk > max_blocks) nblk = max_blocks;
+    k_slices_core<NB, R, J><<<nblk, kCoreSliceThreads, smem, st>>>(g, partials);
+    return nblk;
+}
+
+template <typename F>
+static void dispatch_nb(int N, F &&f) {
+    // the template argument is the number of other-mode slots (>= N - 1)
+    if (N <= 3) f(ic<2>{});
+    else if (N <= 4) f(ic<3>{});
+    else if (N <= 8) f(ic<7>{});
+    else f(ic<15>{});
+}
+
+cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
+                                 float *maps, int J, int R, cudaStream_t st, int sms,
+                                 int64_t *launches) {
+    SliceArgs g{};
+    g.a = a;
+    g.row_ptr = row_ptr;
+    g.W = W;
+    g.Lseq = Lseq;
+    g.ntiles = (a.nnz + W - 1) / W;
+    g.maps = maps;
+    dispatch_nb(a.N, [&](auto nb_c) {
+        constexpr int NB = decltype(nb_c)::value;
+        dispatch_rj(R, J, [&](auto r_c, auto j_c) {
+            factor_slices_t<NB, decltype(r_c)::value, decltype(j_c)::value>(g, maps != nullptr, st,
+                                                                             sms, launches);
+        });
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
+                               float *partials, int max_blocks, cudaStream_t st, int sms,
+                               int64_t *launches) {
+    SliceArgs g{};
+    g.a = a;
+    g.row_ptr = row_ptr;
+    g.W = W;
+    g.Lseq = 0;
+    g.ntiles = (a.count + W - 1) / W;
+    g.maps = nullptr;
+    int nblk = 1;
+    dispatch_nb(a.N, [&](auto nb_c) {
+        constexpr int NB = decltype(nb_c)::value;
+        dispatch_rj(R, J, [&](auto r_c, auto j_c) {
+            nblk = core_slices_t<NB, decltype(r_c)::value, decltype(j_c)::value>(
+                g, partials, max_blocks, st, sms);
+        });
+    });
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 2;
+    return launch_core_apply(a.B, partials, nblk, J * R, a.count, a.lr, a.lam, st);
+}
+
+}  // namespace sft

@@ -36,6 +36,8 @@ struct sft_ctx {
     int64_t det_max_chunks = 0;
     int jmax = 0;
     int64_t launches = 0;
+    int64_t slice_tile = 0;        // 0 = automatic
+    int64_t slice_max_direct = 0;  // 0 = automatic
     std::string last_error;
 };
 
@@ -144,6 +146,14 @@ PassArgs pass_args(const sft_ctx *c, int mode, const int32_t *const *idx, const 
     if (mode >= 0) {
         a.A = c->A[mode];
         a.B = c->B[mode];
+        int q = 0;
+        for (int k = 0; k < c->N; ++k) {
+            if (k == mode) continue;
+            a.oidx[q] = idx[k];
+            a.oC[q] = c->C[k];
+            a.odims[q] = (int32_t)c->dims[k];
+            ++q;
+        }
     }
     a.lr = lr;
     a.lam = lam;
@@ -382,6 +392,111 @@ sft_status sft_epoch(sft_ctx *c, const int32_t *const *idx, const float *val, in
         st = sft_refresh_C(c, n);
         if (st != SFT_OK) return st;
     }
+    return SFT_OK;
+}
+
+// ----------------------------------------------------------------------------- slices
+
+static int64_t slice_W(const sft_ctx *c, int64_t nnz) {
+    return c->slice_tile > 0 ? c->slice_tile : slice_tile_length(nnz, c->sms);
+}
+
+static int64_t slice_Lseq(const sft_ctx *c, int64_t W) {
+    if (c->slice_max_direct > 0) return c->slice_max_direct;
+    if (c->slice_max_direct < 0) return 0;
+    const int64_t L = 8 * W;
+    return L < 2048 ? 2048 : L;
+}
+
+size_t sft_slices_scratch_bytes(int64_t nnz) {
+    if (nnz < 0) return 0;
+    return (size_t)slice_sort_length(nnz) * sizeof(unsigned long long);
+}
+
+sft_status sft_group_slices(sft_ctx *c, int32_t mode, const int32_t *const *idx, const float *val,
+                            const uint32_t *perm, int64_t nnz, int32_t *const *out_idx,
+                            float *out_val, int32_t *out_row_ptr, void *scratch,
+                            size_t scratch_bytes) {
+    if (!c) return SFT_EINVAL;
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    sft_status st = check_set(c, idx, val, nnz);
+    if (st != SFT_OK) return st;
+    if (!out_idx || !out_val || !out_row_ptr) return fail(c, SFT_EINVAL, "output arrays are NULL");
+    for (int k = 0; k < c->N; ++k)
+        if (!out_idx[k]) return fail(c, SFT_EINVAL, "out_idx[k] is NULL");
+    if (!scratch || scratch_bytes < sft_slices_scratch_bytes(nnz) || ((uintptr_t)scratch & 15u))
+        return fail(c, SFT_EINVAL, "scratch missing, misaligned or smaller than sft_slices_scratch_bytes");
+    PassArgs a = pass_args(c, mode, idx, val, perm, nnz, 0.f, 0.f);
+    cudaError_t e = launch_group_slices(a, out_idx, out_val, out_row_ptr,
+                                        (unsigned long long *)scratch, c->stream, c->sms,
+                                        &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slice layout launch");
+    return SFT_OK;
+}
+
+size_t sft_slices_workspace_bytes(const sft_ctx *c, int32_t mode, int64_t nnz) {
+    if (!c || mode < 0 || mode >= c->N || nnz < 0) return 0;
+    const int64_t W = slice_W(c, nnz);
+    const int64_t ntiles = (nnz + W - 1) / W;
+    const int64_t J = c->J[mode];
+    return (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * (size_t)(J * J + J) * sizeof(float);
+}
+
+static sft_status check_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
+                               const float *sval, const int32_t *row_ptr, int64_t nnz) {
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    sft_status st = check_set(c, sidx, sval, nnz);
+    if (st != SFT_OK) return st;
+    if (!row_ptr) return fail(c, SFT_EINVAL, "row_ptr is NULL");
+    return SFT_OK;
+}
+
+sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
+                                     const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                     float lr, float lambda, void *workspace,
+                                     size_t workspace_bytes) {
+    if (!c) return SFT_EINVAL;
+    sft_status st = check_slices(c, mode, sidx, sval, row_ptr, nnz);
+    if (st != SFT_OK) return st;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (nnz == 0) return SFT_OK;
+    if (!workspace || workspace_bytes < sft_slices_workspace_bytes(c, mode, nnz) ||
+        ((uintptr_t)workspace & 15u))
+        return fail(c, SFT_EINVAL, "workspace missing, misaligned or smaller than sft_slices_workspace_bytes");
+    PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
+    const int64_t W = slice_W(c, nnz);
+    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, W), (float *)workspace,
+                                         c->J[mode], c->R, c->stream, c->sms, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
+    return SFT_OK;
+}
+
+sft_status sft_update_core_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
+                                  const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                  int64_t batch, float lr, float lambda) {
+    if (!c) return SFT_EINVAL;
+    sft_status st = check_slices(c, mode, sidx, sval, row_ptr, nnz);
+    if (st != SFT_OK) return st;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
+    if (nnz == 0) return SFT_OK;
+    PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
+    for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
+        a.base = b0;
+        a.count = nnz - b0 < batch ? nnz - b0 : batch;
+        cudaError_t e = launch_core_slices(a, row_ptr, slice_W(c, a.count), c->J[mode], c->R,
+                                           c->core_partials, c->core_max_blocks, c->stream, c->sms,
+                                           &c->launches);
+        if (e != cudaSuccess) return cuda_fail(c, e, "slice core launch");
+    }
+    return SFT_OK;
+}
+
+sft_status sft_set_slice_tiling(sft_ctx *c, int64_t tile, int64_t max_direct) {
+    if (!c) return SFT_EINVAL;
+    if (tile < 0) return fail(c, SFT_EINVAL, "tile must be >= 0");
+    c->slice_tile = tile;
+    c->slice_max_direct = max_direct;  // < 0: every crossing slice goes through maps
     return SFT_OK;
 }
 

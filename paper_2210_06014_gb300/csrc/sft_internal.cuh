@@ -32,6 +32,10 @@ struct PassArgs {
     float *B;                       // B^(n), J_n x R
     float lr, lam;
     int *err;                       // device error flag
+    // the N-1 modes other than n, in ascending order (set when n >= 0)
+    const int32_t *oidx[kMaxOrder];
+    const float *oC[kMaxOrder];
+    int32_t odims[kMaxOrder];
 };
 
 // Workspace pieces used by the deterministic factor path.
@@ -55,6 +59,20 @@ cudaError_t launch_factor_det(const PassArgs &a, int J, int R, const DetFactorWs
 cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nblk,
                         cudaStream_t st);
 int core_blocks_for(int64_t count, int sms);
+cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
+                              float lr, float lam, cudaStream_t st);
+// slice (CSF) layout and the passes over it
+int64_t slice_sort_length(int64_t nnz);
+int slice_tile_length(int64_t nnz, int sms);
+cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
+                                int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
+                                int sms, int64_t *launches);
+cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
+                                 float *maps, int J, int R, cudaStream_t st, int sms,
+                                 int64_t *launches);
+cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
+                               float *partials, int max_blocks, cudaStream_t st, int sms,
+                               int64_t *launches);
 cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, double *out2,
                         cudaStream_t st);
 int loss_blocks_for(int64_t count, int sms);
@@ -105,6 +123,39 @@ __device__ __forceinline__ void load_run(const float *p, float (&r)[L]) {
         r[0] = v.x; r[1] = v.y;
     } else {
         r[0] = *p;
+    }
+}
+
+// Lane mask of the aligned T-lane group that contains `lane`.
+template <int T>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    if constexpr (T == 32) return kFull;
+    else return ((1u << T) - 1u) << (lane & ~(T - 1));
+}
+
+// Group sum with an explicit member mask (groups of a warp may diverge).
+template <int T>
+__device__ __forceinline__ float group_sum_m(float x, unsigned m) {
+#pragma unroll
+    for (int w = T / 2; w >= 1; w >>= 1) x += __shfl_xor_sync(m, x, w);
+    return x;
+}
+
+template <int T, int L>
+__device__ __forceinline__ void group_reduce_scatter_m(float (&v)[L], int sub, unsigned m) {
+#pragma unroll
+    for (int w = T / 2; w >= 1; w >>= 1) {
+        const int len = (L / T) * 2 * w;
+        const bool upper = (sub & w) != 0;
+#pragma unroll
+        for (int q = 0; q < L / 2; ++q) {
+            if (q < len / 2) {
+                float send = upper ? v[q] : v[q + len / 2];
+                float keep = upper ? v[q + len / 2] : v[q];
+                float recv = __shfl_xor_sync(m, send, w);
+                v[q] = keep + recv;
+            }
+        }
     }
 }
 

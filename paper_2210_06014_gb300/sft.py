@@ -27,7 +27,9 @@ _STATUS = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SF
 
 EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_factors",
             "sft_update_core", "sft_loss", "sft_loss_async", "sft_predict", "sft_epoch", "sft_sync",
-            "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy"]
+            "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy",
+            "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_workspace_bytes",
+            "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling"]
 
 
 class SftError(RuntimeError):
@@ -95,6 +97,20 @@ def load(build_if_missing: bool = True):
     lib.sft_launch_count.restype = i64
     lib.sft_destroy.argtypes = [ctx]
     lib.sft_destroy.restype = None
+    lib.sft_slices_scratch_bytes.argtypes = [i64]
+    lib.sft_slices_scratch_bytes.restype = ctypes.c_size_t
+    lib.sft_group_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, ctypes.POINTER(vp),
+                                     vp, vp, vp, ctypes.c_size_t]
+    lib.sft_group_slices.restype = ctypes.c_int
+    lib.sft_slices_workspace_bytes.argtypes = [ctx, i32, i64]
+    lib.sft_slices_workspace_bytes.restype = ctypes.c_size_t
+    lib.sft_update_factors_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, f32, f32,
+                                              vp, ctypes.c_size_t]
+    lib.sft_update_factors_slices.restype = ctypes.c_int
+    lib.sft_update_core_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32]
+    lib.sft_update_core_slices.restype = ctypes.c_int
+    lib.sft_set_slice_tiling.argtypes = [ctx, i64, i64]
+    lib.sft_set_slice_tiling.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -221,6 +237,66 @@ def sft_destroy(ctx) -> None:
         load().sft_destroy(ctx)
 
 
+def sft_slices_scratch_bytes(nnz: int) -> int:
+    return int(load().sft_slices_scratch_bytes(int(nnz)))
+
+
+def sft_group_slices(ctx, mode, idx, val, perm, nnz, out_idx, out_val, out_row_ptr,
+                     scratch: torch.Tensor) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_group_slices(ctx, int(mode), _ptr_array(idx), _ptr(val), _ptr(perm),
+                                          int(nnz), _ptr_array(out_idx), _ptr(out_val),
+                                          _ptr(out_row_ptr), _ptr(scratch),
+                                          scratch.numel() * scratch.element_size()),
+           "sft_group_slices")
+
+
+def sft_slices_workspace_bytes(ctx, mode, nnz) -> int:
+    return int(load().sft_slices_workspace_bytes(ctx, int(mode), int(nnz)))
+
+
+def sft_update_factors_slices(ctx, mode, sidx, sval, row_ptr, nnz, lr, lam,
+                              workspace: torch.Tensor) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_update_factors_slices(ctx, int(mode), _ptr_array(sidx), _ptr(sval),
+                                                   _ptr(row_ptr), int(nnz), float(lr), float(lam),
+                                                   _ptr(workspace),
+                                                   workspace.numel() * workspace.element_size()),
+           "sft_update_factors_slices")
+
+
+def sft_update_core_slices(ctx, mode, sidx, sval, row_ptr, nnz, batch, lr, lam) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_update_core_slices(ctx, int(mode), _ptr_array(sidx), _ptr(sval),
+                                                _ptr(row_ptr), int(nnz), int(batch), float(lr),
+                                                float(lam)), "sft_update_core_slices")
+
+
+def sft_set_slice_tiling(ctx, tile: int = 0, max_direct: int = 0) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_set_slice_tiling(ctx, int(tile), int(max_direct)),
+           "sft_set_slice_tiling")
+
+
+class Slices:
+    """The slice layout of one mode (device tensors): idx (N int32 arrays),
+    val (float32) and row_ptr (I_n + 1 int32), built by sft_group_slices."""
+
+    def __init__(self, dec: "Decomposition", mode: int, idx, val, perm=None):
+        nnz = val.numel()
+        dev = val.device
+        self.mode = mode
+        self.nnz = nnz
+        self.idx = [torch.empty(nnz, dtype=torch.int32, device=dev) for _ in idx]
+        self.val = torch.empty(nnz, dtype=torch.float32, device=dev)
+        self.row_ptr = torch.empty(dec.dims[mode] + 1, dtype=torch.int32, device=dev)
+        scratch = torch.empty(max(16, sft_slices_scratch_bytes(nnz)), dtype=torch.uint8,
+                              device=dev)
+        sft_group_slices(dec.ctx, mode, idx, val, perm, nnz, self.idx, self.val, self.row_ptr,
+                         scratch)
+        self._scratch = scratch  # kept alive until the enqueued work has run
+
+
 # ----------------------------------------------------------------------------- owner object
 
 
@@ -273,6 +349,25 @@ class Decomposition:
               batch_core=4096, lr_A=0.01, lam_A=0.01, lr_B=0.01, lam_B=0.01):
         sft_epoch(self.ctx, idx, val, val.numel(), perm_factor, perm_core, batch_factor,
                   batch_core, lr_A, lam_A, lr_B, lam_B)
+
+    def slices(self, mode, idx, val, perm=None) -> Slices:
+        return Slices(self, mode, idx, val, perm)
+
+    def set_slice_tiling(self, tile: int = 0, max_direct: int = 0):
+        sft_set_slice_tiling(self.ctx, tile, max_direct)
+
+    def update_factors_slices(self, sl: Slices, lr=0.01, lam=0.01):
+        need = max(16, sft_slices_workspace_bytes(self.ctx, sl.mode, sl.nnz))
+        ws = getattr(self, "_slice_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=sl.val.device)
+            self._slice_ws = ws
+        sft_update_factors_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, lr, lam,
+                                  ws)
+
+    def update_core_slices(self, sl: Slices, batch=None, lr=0.01, lam=0.01):
+        sft_update_core_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz,
+                               batch or sl.nnz, lr, lam)
 
     def loss(self, idx, val):
         return sft_loss(self.ctx, idx, val, val.numel())

@@ -1,0 +1,225 @@
+"""GPU parity of the slice-layout passes (CSF slices of one mode) against the
+FP64 oracle, through the C ABI.
+
+The factor pass on a slice layout runs every slice element by element in visit
+order; since slices of one mode do not interact during a factor pass, it must
+equal the oracle's element-by-element pass (batch 1) over the permutation
+that built the layout.  Long slices split into affine maps are forced on with
+small tiles.  The core pass over the layout is compared with the oracle's core
+pass over the same order.
+"""
+import numpy as np
+import pytest
+import torch
+
+from parity_util import (TOL32, assert_within, core_step_scale, np_idx, rel_fro, small_tensor,
+                         to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sft():
+    from paper_2210_06014_gb300 import build, sft as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def perm_of(seed, epoch, phase, mode, n):
+    from paper_2210_06014_gb300 import synth
+    return synth.pass_permutation(seed, epoch, phase, mode, n)
+
+
+def slice_order(idx_np, n, perm):
+    """Storage indices in slice order: sort visit positions by (i_n, position)."""
+    rows = idx_np[n][perm]
+    pos = np.arange(len(perm))
+    order = np.lexsort((pos, rows))
+    return perm[order], rows[order]
+
+
+@pytest.fixture(scope="module")
+def skewed():
+    """A small Netflix-shaped tensor: Zipf(1.1) user / item modes (heavy slices)."""
+    from paper_2210_06014_gb300 import synth
+    spec = synth.spec_ratings(nnz=400_000, dims=(20_000, 3_000, 500))
+    return synth.make_tensor(spec)
+
+
+def test_group_slices_layout(sft):
+    T = small_tensor()
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    for n in range(3):
+        perm = perm_of(5, 0, 0, n, T.nnz)
+        sl = dec.slices(n, idx, val, perm.cuda())
+        dec.sync(60_000)
+        order, rows = slice_order(ix, n, perm.numpy().astype(np.int64))
+        for k in range(3):
+            assert np.array_equal(sl.idx[k].cpu().numpy(), ix[k][order])
+        assert np.array_equal(sl.val.cpu().numpy(), T.val.numpy()[order])
+        want_ptr = np.searchsorted(rows, np.arange(T.spec.dims[n] + 1), side="left")
+        assert np.array_equal(sl.row_ptr.cpu().numpy(), want_ptr)
+
+
+@pytest.mark.parametrize("tiling", [(0, 0), (64, -1), (64, 1 << 30), (7, -1)])
+def test_factor_slices_equal_sequential_pass(sft, oracle_mod, tiling):
+    """Slice pass == oracle element-by-element pass over the same permutation,
+    for every mode and with the long-slice maps forced on or off."""
+    T = small_tensor()
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    dec.set_slice_tiling(*tiling)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        perm = perm_of(7, 0, 0, n, T.nnz)
+        A0 = dec.A[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, perm.cuda())
+        dec.update_factors_slices(sl, lr=0.05, lam=0.01)
+        dec.sync(60_000)
+        ref.factor_pass(n, ix, T.val.numpy(), perm=perm.numpy().astype(np.uint32), batch=1,
+                        lr=0.05, lam=0.01)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
+        assert rel_fro(got, ref.A[n]) < TOL32, n
+        # keep both sides on the same parameters for the next mode
+        dec.A[n].copy_(torch.from_numpy(ref.A[n].astype(np.float32)))
+        dec.refresh(n)
+        ref.A[n] = ref.A[n].astype(np.float32).astype(np.float64)
+        ref.refresh(n)
+
+
+def test_factor_slices_skewed_tensor(sft, oracle_mod, skewed):
+    """Heavy Zipf slices (tens of thousands of nonzeros) go through the map
+    path; the pass still equals the sequential oracle pass."""
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    counts = np.bincount(ix[0], minlength=T.spec.dims[0])
+    assert counts.max() > 10_000
+    for n in range(3):
+        A0 = dec.A[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, None)
+        dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+        dec.sync(60_000)
+        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got))
+        assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
+        assert rel_fro(got, ref.A[n]) < TOL32, n
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_core_slices_one_step_gradient(sft, oracle_mod, n):
+    """Whole-pass core step on the layout (Algorithm 5) with lr = 1: B moves by
+    G / nnz - lam B."""
+    T = small_tensor()
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    lr, lam = 1.0, 0.01
+    dec = sft.Decomposition(T.A0, T.B0)
+    B_before = dec.B[n].cpu().numpy().astype(np.float64)
+    sl = dec.slices(n, idx, val, None)
+    dec.update_core_slices(sl, batch=T.nnz, lr=lr, lam=lam)
+    dec.sync(60_000)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    ref.core_pass(n, ix, T.val.numpy(), batch=T.nnz, lr=lr, lam=lam)
+    got = dec.B[n].cpu().numpy().astype(np.float64) - B_before
+    want = ref.B[n] - B_before
+    scale = core_step_scale(ref.A, [b.numpy().astype(np.float64) for b in T.B0], n, ix,
+                            T.val.numpy(), np.arange(T.nnz), lr, lam)
+    assert_within(got, want, scale + 1e-2 * np.abs(ref.B[n]), what=f"step B^({n})")
+    assert rel_fro(got, want) < TOL32
+
+
+def test_core_slices_minibatches(sft, oracle_mod):
+    """Minibatches of 4096 consecutive layout positions, the last one ragged."""
+    T = small_tensor()
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    n = 1
+    perm = perm_of(9, 0, 1, n, T.nnz)
+    dec = sft.Decomposition(T.A0, T.B0)
+    sl = dec.slices(n, idx, val, perm.cuda())
+    dec.update_core_slices(sl, batch=4096, lr=0.05, lam=0.01)
+    dec.sync(60_000)
+    order, _ = slice_order(ix, n, perm.numpy().astype(np.int64))
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    ref.core_pass(n, ix, T.val.numpy(), perm=order.astype(np.uint32), batch=4096, lr=0.05,
+                  lam=0.01)
+    B0 = T.B0[n].numpy().astype(np.float64)
+    got = dec.B[n].cpu().numpy().astype(np.float64)
+    assert rel_fro(got - B0, ref.B[n] - B0) < 1e-4
+    assert rel_fro(got, ref.B[n]) < TOL32
+
+
+def _slice_epochs(sft, oracle_mod, T, epochs, lr=0.01, core_batch=4096):
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    xv = T.val.numpy()
+    dec = sft.Decomposition(T.A0, T.B0)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    got, want = [], []
+    N = len(ix)
+    for ep in range(epochs):
+        pf = [perm_of(0, ep, 0, n, T.nnz) for n in range(N)]
+        pc = [perm_of(0, ep, 1, n, T.nnz) for n in range(N)]
+        for n in range(N):
+            sl = dec.slices(n, idx, val, pf[n].cuda())
+            dec.update_factors_slices(sl, lr=lr, lam=0.01)
+            dec.refresh(n)
+        for n in range(N):
+            sl = dec.slices(n, idx, val, pc[n].cuda())
+            dec.update_core_slices(sl, batch=core_batch, lr=lr, lam=0.01)
+            dec.refresh(n)
+        got.append(dec.rmse(idx, val))
+        core_orders = [slice_order(ix, n, pc[n].numpy().astype(np.int64))[0].astype(np.uint32)
+                       for n in range(N)]
+        ref.epoch(ix, xv, [p.numpy().astype(np.uint32) for p in pf], core_orders,
+                  batch_factor=1, batch_core=core_batch, lr_A=lr, lam_A=0.01, lr_B=lr,
+                  lam_B=0.01)
+        want.append(ref.rmse(ix, xv))
+    return np.array(got), np.array(want), dec, ref
+
+
+def test_slice_epochs_rmse(sft, oracle_mod):
+    """5 epochs of Algorithm 2 on slice layouts (factor rows element by
+    element, core minibatches of 4096): training RMSE within 1 % per epoch."""
+    T = small_tensor()
+    got, want, dec, ref = _slice_epochs(sft, oracle_mod, T, 5)
+    np.testing.assert_allclose(got, want, rtol=0.01)
+    for n in range(3):
+        assert rel_fro(dec.A[n].cpu().numpy(), ref.A[n]) < 1e-4
+        assert rel_fro(dec.B[n].cpu().numpy(), ref.B[n]) < 1e-4
+
+
+def test_slice_epochs_skewed_rmse(sft, oracle_mod, skewed):
+    """Two epochs on the Zipf tensor with one core update per pass: the slice
+    path stays finite and tracks the oracle (the minibatch and Hogwild rules
+    diverge here at this learning rate)."""
+    got, want, _, _ = _slice_epochs(sft, oracle_mod, skewed, 2, lr=0.01, core_batch=skewed.nnz)
+    assert np.all(np.isfinite(want))
+    np.testing.assert_allclose(got, want, rtol=0.01)
+
+
+def test_slices_bitwise_reproducible(sft, skewed):
+    T = skewed
+    idx, val = to_dev(T)
+    outs = []
+    for _ in range(2):
+        dec = sft.Decomposition(T.A0, T.B0)
+        for n in range(3):
+            sl = dec.slices(n, idx, val, None)
+            dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+            dec.refresh(n)
+            dec.update_core_slices(sl, lr=0.01, lam=0.01)
+            dec.refresh(n)
+        dec.sync(60_000)
+        outs.append([t.clone() for t in dec.A + dec.B])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
