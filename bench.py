@@ -256,6 +256,8 @@ def main():
         slices = [dec.slices(n, idx, val, None) for n in range(N)]
         torch.cuda.synchronize()
         layout_s = time.perf_counter() - t0
+        for sl in slices:
+            sl._scratch = None  # sort keys are no longer needed
         touched = [int((sl.row_ptr[1:] > sl.row_ptr[:-1]).sum()) for sl in slices]
         rows_per_nnz = sum(touched) / (N * nnz)
 
