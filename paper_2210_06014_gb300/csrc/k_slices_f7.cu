@@ -1,0 +1,14 @@
+// k_slices_f7.cu -- factor-pass slice kernels for orders up to 8.
+#include "slices_impl.cuh"
+
+namespace sft {
+
+void factor_slices_no7(const SliceArgs &g, int R, int J, bool with_maps, cudaStream_t st,
+                         int sms, int64_t *launches) {
+    dispatch_rj(R, J, [&](auto r_c, auto j_c) {
+        factor_slices_t<7, decltype(r_c)::value, decltype(j_c)::value>(g, with_maps, st, sms,
+                                                                         launches);
+    });
+}
+
+}  // namespace sft

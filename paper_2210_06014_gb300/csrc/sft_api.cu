@@ -401,11 +401,18 @@ static int64_t slice_W(const sft_ctx *c, int64_t nnz) {
     return c->slice_tile > 0 ? c->slice_tile : slice_tile_length(nnz, c->sms);
 }
 
-static int64_t slice_Lseq(const sft_ctx *c, int64_t W) {
+// Longest crossing slice run as one element-by-element chain: about a third of
+// the pass's streaming time (bytes at ~6.8 TB/s) at ~0.4 us per dependent step,
+// so chains stay off the critical path; longer slices are split into maps.
+static int64_t slice_Lseq(const sft_ctx *c, int64_t W, int64_t nnz) {
     if (c->slice_max_direct > 0) return c->slice_max_direct;
     if (c->slice_max_direct < 0) return 0;
-    const int64_t L = 8 * W;
-    return L < 2048 ? 2048 : L;
+    const double bytes = (double)nnz * (4.0 * c->N + 4.0 + 4.0 * (c->N - 1) * c->R);
+    const double pass_us = bytes / 6.8e6;
+    int64_t L = (int64_t)(pass_us / 3.0 / 0.4);
+    if (L < 2 * W) L = 2 * W;
+    if (L > (1 << 20)) L = 1 << 20;
+    return L;
 }
 
 size_t sft_slices_scratch_bytes(int64_t nnz) {
@@ -465,7 +472,7 @@ sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *co
         return fail(c, SFT_EINVAL, "workspace missing, misaligned or smaller than sft_slices_workspace_bytes");
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
-    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, W), (float *)workspace,
+    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, W, nnz), (float *)workspace,
                                          c->J[mode], c->R, c->stream, c->sms, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
     return SFT_OK;

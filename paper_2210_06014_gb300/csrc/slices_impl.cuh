@@ -1,181 +1,13 @@
-// k_slices.cu -- the factor and core passes over nonzeros grouped into the
-// mode-n slices of the tensor (all nonzeros that share i_n, kept in visit
-// order), the CSF layout of Section "Tensor Storage Format".
-//
-// Layout.  k_slice_keys / k_bitonic_* / k_slice_gather / k_slice_rowptr sort
-// the visit positions by (i_n, position) -- a bitonic sort of unique 64-bit
-// keys, so the order inside a slice is the visit order -- and copy the COO
-// arrays into that order; row_ptr[i] is the first position of slice i.
-//
-// Factor pass (Eq. (9)-(10), element by element as in Algorithm 4).  During a
-// factor pass over mode n a nonzero reads and writes only a_{i_n}; slices are
-// independent, and running every slice's nonzeros one after another in visit
-// order reproduces the element-by-element rule exactly.  Work is cut into
-// tiles of W consecutive positions, one lane group (T = R/4 lanes) per tile:
-//   - a slice that lies inside a tile is run directly: the row stays in
-//     registers, each nonzero does e = x - a.(B p), a += lr (e v - lambda a);
-//   - a slice that crosses tile boundaries and has at most Lseq nonzeros is run
-//     directly, whole, by the group that owns its first boundary;
-//   - a longer slice is split at the tile boundaries.  One step is the affine
-//     map a -> M_t a + c_t with M_t = (1 - lr lambda) I - lr v v^T and
-//     c_t = lr x v, so each piece is composed into one map (M, c) in parallel
-//     (k_slices_maps) and k_slices_combine applies the pieces to the row in
-//     order.  This is the same recurrence, re-associated.
-// Nothing is atomic and the result is bitwise reproducible.
-//
-// Core pass (Eq. (9), (11), Algorithm 5).  With A^(n) fixed,
-//   G = sum_s e_s a_{i_n(s)} p_s^T = sum_slices a_i (sum_{s in slice} e_s p_s)^T,
-// so a group keeps q = sum e_s p_s over the run of a slice inside its tile and
-// adds a_i q^T to its shared-memory tile of G once per run.  x^_s = (B^T a).p_s
-// uses w = B^T a computed once per run.
+// slices_impl.cuh -- kernels of the passes over the slice (CSF) layout; see
+// k_slices_layout.cu for the layout, the description of the method and the
+// launchers.  Included by the per-order translation units k_slices_f*.cu /
+// k_slices_c*.cu, which instantiate them for one bound on the order.
+#pragma once
+
 #include "dispatch.cuh"
 #include "sft_internal.cuh"
 
 namespace sft {
-
-// ============================================================================ layout
-constexpr int kSortBlock = 2048;
-
-__global__ void k_slice_keys(const int32_t *__restrict__ rowidx, const uint32_t *__restrict__ perm,
-                             int64_t nnz, int32_t In, unsigned long long *__restrict__ keys,
-                             int64_t P, int *err) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
-        unsigned long long key = ~0ull;
-        if (i < nnz) {
-            int64_t s = i;
-            uint32_t row = (uint32_t)In;  // invalid samples sort after every slice
-            bool ok = true;
-            if (perm) {
-                const uint32_t q = perm[i];
-                if ((int64_t)q >= nnz) {
-                    atomicOr(err, kErrPerm);
-                    ok = false;
-                } else {
-                    s = q;
-                }
-            }
-            if (ok) {
-                const uint32_t r = (uint32_t)rowidx[s];
-                if (r >= (uint32_t)In) atomicOr(err, kErrIndex);
-                else row = r;
-            }
-            key = ((unsigned long long)row << 32) | (unsigned long long)i;
-        }
-        keys[i] = key;
-    }
-}
-
-// Bitonic stages with partner distance < kSortBlock, in shared memory.  For
-// k_lo == 2 it sorts every block fully (k = 2 .. kSortBlock); otherwise it
-// finishes the merge of size k_lo (== k_hi) from distance kSortBlock/2 down.
-__global__ void __launch_bounds__(kSortBlock / 2) k_bitonic_local(unsigned long long *keys,
-                                                                   int64_t k_lo, int64_t k_hi) {
-    __shared__ unsigned long long s[kSortBlock];
-    const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    s[t] = keys[base + t];
-    s[t + kSortBlock / 2] = keys[base + t + kSortBlock / 2];
-    __syncthreads();
-    for (int64_t k = k_lo; k <= k_hi; k <<= 1) {
-        for (int j = (int)(k / 2 < kSortBlock / 2 ? k / 2 : kSortBlock / 2); j > 0; j >>= 1) {
-            const int i = 2 * j * (t / j) + (t % j);
-            const bool up = ((base + i) & k) == 0;
-            const unsigned long long x = s[i], y = s[i + j];
-            if ((x > y) == up) {
-                s[i] = y;
-                s[i + j] = x;
-            }
-            __syncthreads();
-        }
-    }
-    keys[base + t] = s[t];
-    keys[base + t + kSortBlock / 2] = s[t + kSortBlock / 2];
-}
-
-__global__ void k_bitonic_global(unsigned long long *keys, int64_t P, int64_t k, int64_t j) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P / 2; t += stride) {
-        const int64_t i = 2 * j * (t / j) + (t % j);
-        const bool up = (i & k) == 0;
-        const unsigned long long x = keys[i], y = keys[i + j];
-        if ((x > y) == up) {
-            keys[i] = y;
-            keys[i + j] = x;
-        }
-    }
-}
-
-struct SliceOut {
-    int32_t *idx[kMaxOrder];
-    float *val;
-};
-
-__global__ void k_slice_gather(PassArgs a, const unsigned long long *__restrict__ keys, SliceOut o) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.nnz; t += stride) {
-        const unsigned long long key = keys[t];
-        const uint32_t row = (uint32_t)(key >> 32);
-        const int64_t pos = (int64_t)(key & 0xffffffffu);
-        if (row >= (uint32_t)a.dims[a.n]) {
-            for (int k = 0; k < a.N; ++k) o.idx[k][t] = -1;
-            o.val[t] = 0.f;
-            continue;
-        }
-        const int64_t s = a.perm ? (int64_t)a.perm[pos] : pos;
-        for (int k = 0; k < a.N; ++k) o.idx[k][t] = a.idx[k][s];
-        o.val[t] = a.val[s];
-    }
-}
-
-__global__ void k_slice_rowptr(const unsigned long long *__restrict__ keys, int64_t nnz, int32_t In,
-                               int32_t *__restrict__ row_ptr) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= In; r += stride) {
-        int64_t lo = 0, hi = nnz;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)(keys[mid] >> 32) < r) lo = mid + 1; else hi = mid;
-        }
-        row_ptr[r] = (int32_t)lo;
-    }
-}
-
-int64_t slice_sort_length(int64_t nnz) {
-    int64_t P = kSortBlock;
-    while (P < nnz) P <<= 1;
-    return P;
-}
-
-cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
-                                int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
-                                int sms, int64_t *launches) {
-    const int64_t P = slice_sort_length(a.nnz);
-    const int th = 256;
-    auto grid = [&](int64_t n) {
-        int64_t b = (n + th - 1) / th;
-        const int64_t cap = (int64_t)sms * 16;
-        return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-    };
-    k_slice_keys<<<grid(P), th, 0, st>>>(a.idx[a.n], a.perm, a.nnz, a.dims[a.n], keys, P, a.err);
-    k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, 2, kSortBlock);
-    *launches += 2;
-    for (int64_t k = 2 * kSortBlock; k <= P; k <<= 1) {
-        for (int64_t j = k / 2; j >= kSortBlock; j >>= 1) {
-            k_bitonic_global<<<grid(P / 2), th, 0, st>>>(keys, P, k, j);
-            *launches += 1;
-        }
-        k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, k, k);
-        *launches += 1;
-    }
-    SliceOut o{};
-    for (int k = 0; k < a.N; ++k) o.idx[k] = out_idx[k];
-    o.val = out_val;
-    k_slice_gather<<<grid(a.nnz), th, 0, st>>>(a, keys, o);
-    k_slice_rowptr<<<grid((int64_t)a.dims[a.n] + 1), th, 0, st>>>(keys, a.nnz, a.dims[a.n], row_ptr);
-    *launches += 2;
-    return cudaGetLastError();
-}
 
 // ============================================================================ shared pieces
 // NO = number of "other" mode slots (modes != n), a compile-time bound on N-1.
@@ -474,49 +306,8 @@ __global__ void __launch_bounds__(kSliceThreads) k_slices_maps(SliceArgs g) {
             } else if (side == 1 && after && !before) {
                 compose_map<NB, R, J>(g, sB, max(s, p0), p1, sub, m,
                                       g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
-            } else if (side == 1 && after && before && s >= p0) {
-                // unreachable: a run that starts before the tile is handled by side 0
             }
         }
-    }
-}
-
-// One group per long crossing slice: applies its maps in tile order.
-template <int R, int J>
-__global__ void __launch_bounds__(kSliceThreads) k_slices_combine(SliceArgs g) {
-    constexpr int T = R / 4;
-    constexpr int JL = J / T;
-    constexpr int MS = J * J + J;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (T - 1);
-    const unsigned m = group_mask<T>(lane);
-    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
-    for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
-         item < g.ntiles - 1; item += groups) {
-        int32_t r;
-        int64_t s, e;
-        if (!first_boundary_slice(g, item + 1, r, s, e) || e - s <= g.Lseq) continue;
-        float *arow = g.a.A + (int64_t)r * J + sub * JL;
-        float av[JL];
-        load_run<JL>(arow, av);
-        const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
-        for (int64_t t = t0; t <= t1; ++t) {
-            const int slot = s < t * g.W ? 0 : 1;
-            const float *mp = g.maps + (t * 2 + slot) * (int64_t)MS;
-            float full[J];
-#pragma unroll
-            for (int k = 0; k < J; ++k) full[k] = __shfl_sync(m, av[k % JL], k / JL, T);
-#pragma unroll
-            for (int q = 0; q < JL; ++q) {
-                const float *row = mp + (sub * JL + q) * J;
-                float acc = __ldcg(mp + J * J + sub * JL + q);
-#pragma unroll
-                for (int k = 0; k < J; ++k) acc = fmaf(__ldcg(row + k), full[k], acc);
-                av[q] = acc;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < JL; ++q) arow[q] = av[q];
     }
 }
 
@@ -621,16 +412,8 @@ __global__ void __launch_bounds__(kCoreSliceThreads) k_slices_core(SliceArgs g,
     }
 }
 
-// ============================================================================ launchers
-int slice_tile_length(int64_t nnz, int sms) {
-    int64_t W = nnz / ((int64_t)sms * 2048);
-    if (W < 32) W = 32;
-    if (W > 2048) W = 2048;
-    return (int)W;
-}
-
 template <typename K>
-static int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block, int64_t items,
+inline int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block, int64_t items,
                     int sms) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
@@ -643,8 +426,8 @@ static int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block,
 }
 
 template <int NB, int R, int J>
-static void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st, int sms,
-                            int64_t *launches) {
+void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st, int sms,
+                     int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
     const int gd = grid_for(k_slices_direct<NB, R, J>, kSliceThreads, 0, gpb, 2 * g.ntiles - 1, sms);
     k_slices_direct<NB, R, J><<<gd, kSliceThreads, 0, st>>>(g);
@@ -652,14 +435,12 @@ static void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st,
     if (with_maps && g.ntiles > 1) {
         const int gm = grid_for(k_slices_maps<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
         k_slices_maps<NB, R, J><<<gm, kSliceThreads, 0, st>>>(g);
-        const int gc = grid_for(k_slices_combine<R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
-        k_slices_combine<R, J><<<gc, kSliceThreads, 0, st>>>(g);
-        *launches += 2;
+        *launches += 1;
     }
 }
 
 template <int NB, int R, int J>
-static int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStream_t st,
+int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStream_t st,
                          int sms) {
     constexpr int T = R / 4;
     const size_t smem = (size_t)(1 + kCoreSliceThreads / T) * J * R * sizeof(float);
@@ -672,57 +453,17 @@ static int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cu
     return nblk;
 }
 
-template <typename F>
-static void dispatch_nb(int N, F &&f) {
-    // the template argument is the number of other-mode slots (>= N - 1)
-    if (N <= 3) f(ic<2>{});
-    else if (N <= 4) f(ic<3>{});
-    else if (N <= 8) f(ic<7>{});
-    else f(ic<15>{});
-}
 
-cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, int J, int R, cudaStream_t st, int sms,
-                                 int64_t *launches) {
-    SliceArgs g{};
-    g.a = a;
-    g.row_ptr = row_ptr;
-    g.W = W;
-    g.Lseq = Lseq;
-    g.ntiles = (a.nnz + W - 1) / W;
-    g.maps = maps;
-    dispatch_nb(a.N, [&](auto nb_c) {
-        constexpr int NB = decltype(nb_c)::value;
-        dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-            factor_slices_t<NB, decltype(r_c)::value, decltype(j_c)::value>(g, maps != nullptr, st,
-                                                                             sms, launches);
-        });
-    });
-    return cudaGetLastError();
-}
-
-cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
-                               float *partials, int max_blocks, cudaStream_t st, int sms,
-                               int64_t *launches) {
-    SliceArgs g{};
-    g.a = a;
-    g.row_ptr = row_ptr;
-    g.W = W;
-    g.Lseq = 0;
-    g.ntiles = (a.count + W - 1) / W;
-    g.maps = nullptr;
-    int nblk = 1;
-    dispatch_nb(a.N, [&](auto nb_c) {
-        constexpr int NB = decltype(nb_c)::value;
-        dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-            nblk = core_slices_t<NB, decltype(r_c)::value, decltype(j_c)::value>(
-                g, partials, max_blocks, st, sms);
-        });
-    });
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    *launches += 2;
-    return launch_core_apply(a.B, partials, nblk, J * R, a.count, a.lr, a.lam, st);
-}
+// Per-order wrappers (defined in k_slices_f<NO>.cu / k_slices_c<NO>.cu).
+#define SFT_SLICE_WRAPPERS(NO)                                                              \
+    void factor_slices_no##NO(const SliceArgs &g, int R, int J, bool with_maps,            \
+                              cudaStream_t st, int sms, int64_t *launches);                 \
+    int core_slices_no##NO(const SliceArgs &g, int R, int J, float *partials, int max_blocks, \
+                           cudaStream_t st, int sms);
+SFT_SLICE_WRAPPERS(2)
+SFT_SLICE_WRAPPERS(3)
+SFT_SLICE_WRAPPERS(7)
+SFT_SLICE_WRAPPERS(15)
+#undef SFT_SLICE_WRAPPERS
 
 }  // namespace sft
