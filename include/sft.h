@@ -201,6 +201,41 @@ sft_status sft_update_core_slices(sft_ctx *ctx, int32_t mode, const int32_t *con
  * rounding. */
 sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
 
+/* ---------------------------------------------------------------------------
+ * Factor pass without any device allocation.  The paper has no counterpart to
+ * this call; it exists for callers that cannot allocate device memory -- e.g.
+ * a plugin inside a host application that owns all device memory through its
+ * own pool and forbids cudaMalloc/cudaFree, or a latency-critical loop that
+ * must not allocate -- and so cannot give sft_init a workspace.
+ *
+ * It runs the same deterministic minibatch factor pass as sft_update_factors
+ * with deterministic = 1 (same kernels, same result), taking every operand
+ * directly: the order, mode lengths dims[N], ranks J[N] and R; mode; the
+ * device matrices A_mode (I_mode x J_mode, updated in place), B_mode
+ * (J_mode x R) and C[N] (I_k x R, the cached products); the COO set idx[N],
+ * val, optional perm, nnz; batch, lr, lambda; the cudaStream_t `stream`.
+ * Its scratch (the per-chunk row sums of a minibatch and the bad-data flag) is
+ * a fixed ~529 KB array of device memory inside the library image, kept by
+ * every GPU that loads the library until the process exits; no call allocates,
+ * frees, or calls an allocating routine.
+ *   - batch must be 1..4096 (the scratch holds one minibatch of at most 4096
+ *     nonzeros); a larger batch returns SFT_ENOTSUP and does nothing;
+ *   - the first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream
+ *     capture;
+ *   - all calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must not be issued;
+ *   - the call waits for `stream` and returns SFT_EINVAL if a kernel flagged
+ *     bad data (coordinates out of range, permutation entries >= nnz), which
+ *     was then skipped.
+ * Returns SFT_EINVAL / SFT_ENOTSUP for bad or unsupported arguments before any
+ * launch, SFT_ECUDA on a CUDA error. */
+sft_status sft_update_factors_noalloc(int32_t order, const int64_t *dims, const int32_t *J,
+                                      int32_t R, int32_t mode, float *A_mode, const float *B_mode,
+                                      float *const *C, const int32_t *const *idx, const float *val,
+                                      const uint32_t *perm, int64_t nnz, int64_t batch, float lr,
+                                      float lambda, void *stream);
+
 /* Wait for the stream, at most timeout_ms milliseconds (< 0: no limit).
  * Returns SFT_ETIMEOUT if work is still running, SFT_EINVAL if a kernel
  * flagged bad data (the flag is then cleared), SFT_ECUDA on a CUDA error. */

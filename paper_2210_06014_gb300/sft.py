@@ -29,7 +29,8 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_update_core", "sft_loss", "sft_loss_async", "sft_predict", "sft_epoch", "sft_sync",
             "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy",
             "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_workspace_bytes",
-            "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling"]
+            "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling",
+            "sft_update_factors_noalloc"]
 
 
 class SftError(RuntimeError):
@@ -111,6 +112,10 @@ def load(build_if_missing: bool = True):
     lib.sft_update_core_slices.restype = ctypes.c_int
     lib.sft_set_slice_tiling.argtypes = [ctx, i64, i64]
     lib.sft_set_slice_tiling.restype = ctypes.c_int
+    lib.sft_update_factors_noalloc.argtypes = [
+        i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
+        ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
+    lib.sft_update_factors_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -276,6 +281,21 @@ def sft_set_slice_tiling(ctx, tile: int = 0, max_direct: int = 0) -> None:
     lib = load()
     _check(lib, ctx, lib.sft_set_slice_tiling(ctx, int(tile), int(max_direct)),
            "sft_set_slice_tiling")
+
+
+def sft_update_factors_noalloc(dims, J, R, mode, A_mode, B_mode, C, idx, val, perm, nnz, batch,
+                               lr, lam, stream=None) -> int:
+    """The allocation-free factor pass; returns the sft_status code."""
+    lib = load()
+    dims_a = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    J_a = (ctypes.c_int32 * len(J))(*[int(j) for j in J])
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return int(lib.sft_update_factors_noalloc(len(dims), dims_a, J_a, int(R), int(mode),
+                                              _ptr(A_mode), _ptr(B_mode), _ptr_array(C),
+                                              _ptr_array(idx), _ptr(val), _ptr(perm), int(nnz),
+                                              int(batch), float(lr), float(lam),
+                                              ctypes.c_void_p(stream)))
 
 
 class Slices:
