@@ -7,6 +7,13 @@
 #include "dispatch.cuh"
 #include "sft_internal.cuh"
 
+// Minimum resident blocks per SM requested from the register allocator: the
+// slice kernels are latency bound, so occupancy is traded against a few spills
+// for J <= 16; J = 32 keeps more registers.
+#define SFT_DIRECT_MINB (J >= 32 ? 2 : 4)
+#define SFT_MAPS_MINB (J >= 32 ? 1 : 2)
+#define SFT_CORE_MINB (J >= 32 ? 4 : 8)
+
 namespace sft {
 
 // ============================================================================ shared pieces
@@ -153,7 +160,7 @@ constexpr int kSliceThreads = 256;
 // Items [0, ntiles-1): tile boundaries (whole crossing slices of at most Lseq
 // nonzeros); items [ntiles-1, 2 ntiles - 1): tiles (slices inside the tile).
 template <int NB, int R, int J>
-__global__ void __launch_bounds__(kSliceThreads) k_slices_direct(SliceArgs g) {
+__global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_direct(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
@@ -273,7 +280,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 // before the tile) and last run (if its slice continues after the tile) when
 // that slice is longer than Lseq.
 template <int NB, int R, int J>
-__global__ void __launch_bounds__(kSliceThreads) k_slices_maps(SliceArgs g) {
+__global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_slices_maps(SliceArgs g) {
 constexpr int kCoreSliceThreads = 128;
 
 template <int NB, int R, int J>
-__global__ void __launch_bounds__(kCoreSliceThreads) k_slices_core(SliceArgs g,
+__global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_core(SliceArgs g,
                                                                    float *__restrict__ partials) {
     constexpr int T = R / 4;
     constexpr int GPB = kCoreSliceThreads / T;
