@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
             const float *P = g.maps + (tl * 2 + piece_slot(s, tl, g.W)) * (int64_t)MS;
             for (int q = 0; q < JL; ++q) {
                 const int j = sub * JL + q;
-                for (int k = 0; k < J; ++k) X[j * J + k] = __ldcg(P + j * J + k);
-                X[J * J + j] = __ldcg(P + J * J + j);
+                for (int k = 0; k < J; ++k) X[j * J + k] = __ldg(P + j * J + k);
+                X[J * J + j] = __ldg(P + J * J + j);
             }
             for (int64_t u = tl - 1; u >= t; --u) {
                 P = g.maps + (u * 2 + piece_slot(s, u, g.W)) * (int64_t)MS;
@@ -251,10 +251,10 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
 #pragma unroll 4
                     for (int l = 0; l < J; ++l) {
                         const float xl = X[j * J + l];
-                        nc = fmaf(xl, __ldcg(P + J * J + l), nc);
+                        nc = fmaf(xl, __ldg(P + J * J + l), nc);
 #pragma unroll
                         for (int k4 = 0; k4 < J / 4; ++k4) {
-                            const float4 v = __ldcg(reinterpret_cast<const float4 *>(P + l * J) + k4);
+                            const float4 v = __ldg(reinterpret_cast<const float4 *>(P + l * J) + k4);
                             nr[4 * k4] = fmaf(xl, v.x, nr[4 * k4]);
                             nr[4 * k4 + 1] = fmaf(xl, v.y, nr[4 * k4 + 1]);
                             nr[4 * k4 + 2] = fmaf(xl, v.z, nr[4 * k4 + 2]);

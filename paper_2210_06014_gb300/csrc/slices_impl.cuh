@@ -10,9 +10,9 @@
 // Minimum resident blocks per SM requested from the register allocator: the
 // slice kernels are latency bound, so occupancy is traded against a few spills
 // for J <= 16; J = 32 keeps more registers.
-#define SFT_DIRECT_MINB (J >= 32 ? 2 : 4)
+#define SFT_DIRECT_MINB (J >= 32 ? 2 : 3)
 #define SFT_MAPS_MINB (J >= 32 ? 1 : 2)
-#define SFT_CORE_MINB (J >= 32 ? 4 : 8)
+#define SFT_CORE_MINB (J >= 32 ? 2 : 5)
 
 namespace sft {
 
@@ -68,6 +68,51 @@ __device__ __forceinline__ float4 product(const Rows<NO> &w) {
     return p;
 }
 
+// Prefetch depth of the slice walks: coordinates and cached rows of the next
+// D positions are in flight while the current one is computed.
+template <int NO, int DMAX>
+struct WalkDepth {
+    static constexpr int base = NO <= 2 ? 4 : (NO <= 3 ? 3 : (NO <= 7 ? 2 : 1));
+    static constexpr int value = base < DMAX ? base : DMAX;
+};
+
+// Calls body(x, ok, p) for slice-ordered positions [s0, s1) in order, where p
+// is the lane's 4 entries of prod_{k != n} C^(k)[i_k][:] and ok says whether
+// the position's data was valid.
+template <int NO, int R, int DMAX, typename Body>
+__device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, int sub,
+                                     Body &&body) {
+    constexpr int D = WalkDepth<NO, DMAX>::value;
+    Rows<NO> ring[D];
+    float rx[D];
+    bool rok[D];
+    {
+        Sample<NO> tmp[D];
+#pragma unroll
+        for (int u = 0; u < D; ++u) load_sample<NO>(a, s0 + u, s0 + u < s1, tmp[u]);
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            load_rows<NO, R>(a, tmp[u], sub, ring[u]);
+            rx[u] = tmp[u].x;
+            rok[u] = tmp[u].ok;
+        }
+    }
+    Sample<NO> pend;
+    load_sample<NO>(a, s0 + D, s0 + D < s1, pend);
+    for (int64_t t = s0; t < s1; t += D) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            if (t + u < s1) {
+                body(rx[u], rok[u], product<NO>(ring[u]));
+                load_rows<NO, R>(a, pend, sub, ring[u]);  // position t + u + D
+                rx[u] = pend.x;
+                rok[u] = pend.ok;
+                load_sample<NO>(a, t + u + D + 1, t + u + D + 1 < s1, pend);
+            }
+        }
+    }
+}
+
 struct SliceArgs {
     PassArgs a;              // idx / val in slice order, perm unused
     const int32_t *row_ptr;  // I_n + 1 slice starts
@@ -95,19 +140,7 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
     float av[JL];
     float *arow = a.A + (int64_t)r * J + sub * JL;
     load_run<JL>(arow, av);
-    Sample<NB> c;
-    Rows<NB> w0, w1;
-    load_sample<NB>(a, s0, true, c);
-    load_rows<NB, R>(a, c, sub, w0);
-    float x0 = c.x;
-    bool ok0 = c.ok;
-    load_sample<NB>(a, s0 + 1, s0 + 1 < s1, c);
-    for (int64_t t = s0; t < s1; ++t) {
-        load_rows<NB, R>(a, c, sub, w1);  // position t+1 (identity rows when past the end)
-        const float x1 = c.x;
-        const bool ok1 = c.ok;
-        load_sample<NB>(a, t + 2, t + 2 < s1, c);
-        const float4 p = product<NB>(w0);
+    walk<NB, R, 4>(a, s0, s1, sub, [&](float x, bool ok, const float4 &p) {
         float vp[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -118,15 +151,12 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
         float dot = 0.f;
 #pragma unroll
         for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vp[q], dot);
-        const float e = x0 - group_sum_m<T>(dot, m);
-        if (ok0) {
+        const float e = x - group_sum_m<T>(dot, m);
+        if (ok) {
 #pragma unroll
             for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vp[q] - a.lam * av[q]);
         }
-        w0 = w1;
-        x0 = x1;
-        ok0 = ok1;
-    }
+    });
     if constexpr (JL >= 4) {
 #pragma unroll
         for (int q = 0; q < JL / 4; ++q)
@@ -220,19 +250,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 #pragma unroll
         for (int k = 0; k < J; ++k) M[q][k] = (sub * JL + q == k) ? 1.f : 0.f;
     }
-    Sample<NB> c;
-    Rows<NB> w0, w1;
-    load_sample<NB>(a, s0, true, c);
-    load_rows<NB, R>(a, c, sub, w0);
-    float x0 = c.x;
-    bool ok0 = c.ok;
-    load_sample<NB>(a, s0 + 1, s0 + 1 < s1, c);
-    for (int64_t t = s0; t < s1; ++t) {
-        load_rows<NB, R>(a, c, sub, w1);
-        const float x1 = c.x;
-        const bool ok1 = c.ok;
-        load_sample<NB>(a, t + 2, t + 2 < s1, c);
-        const float4 p = product<NB>(w0);
+    walk<NB, R, 2>(a, s0, s1, sub, [&](float x0, bool ok0, const float4 &p) {
         float v[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -264,10 +282,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
                 cv[q] = fmaf(alpha, cv[q], lv * (x0 - sc));
             }
         }
-        w0 = w1;
-        x0 = x1;
-        ok0 = ok1;
-    }
+    });
 #pragma unroll
     for (int q = 0; q < JL; ++q) {
 #pragma unroll
@@ -373,19 +388,7 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
                 w.w = fmaf(arow[j], b.w, w.w);
             }
             float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
-            Sample<NB> c;
-            Rows<NB> w0, w1;
-            load_sample<NB>(a, pos, true, c);
-            load_rows<NB, R>(a, c, sub, w0);
-            float x0 = c.x;
-            bool ok0 = c.ok;
-            load_sample<NB>(a, pos + 1, pos + 1 < se, c);
-            for (int64_t u = pos; u < se; ++u) {
-                load_rows<NB, R>(a, c, sub, w1);
-                const float x1 = c.x;
-                const bool ok1 = c.ok;
-                load_sample<NB>(a, u + 2, u + 2 < se, c);
-                const float4 p = product<NB>(w0);
+            walk<NB, R, 4>(a, pos, se, sub, [&](float x0, bool ok0, const float4 &p) {
                 const float part = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, w.w * p.w)));
                 const float xh = group_sum_m<T>(part, m);
                 const float ev = ok0 ? x0 - xh : 0.f;
@@ -393,10 +396,7 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
                 qv.y = fmaf(ev, p.y, qv.y);
                 qv.z = fmaf(ev, p.z, qv.z);
                 qv.w = fmaf(ev, p.w, qv.w);
-                w0 = w1;
-                x0 = x1;
-                ok0 = ok1;
-            }
+            });
             // G[j][4 sub .. 4 sub + 3] += a_j q  (the lane's four columns of the group tile)
 #pragma unroll
             for (int j = 0; j < J; ++j) {
