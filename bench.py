@@ -124,7 +124,13 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def dist_setup(args):
+_REDUCE_DEVICE = "cpu"
+
+
+def dist_setup(args=None):
+    """One process per GPU (torchrun env vars); NCCL with GPUs, gloo without.
+    Returns (world, rank, local_rank)."""
+    global _REDUCE_DEVICE
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -132,7 +138,9 @@ def dist_setup(args):
         import torch.distributed as dist
         if torch.cuda.is_available():
             torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+            _REDUCE_DEVICE = "cuda"
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
@@ -145,21 +153,29 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Timing is the slowest rank's (max over ranks)."""
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_REDUCE_DEVICE)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def sum_over_ranks(x, world):
+    """Work is summed over ranks (each rank runs its own replica)."""
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_REDUCE_DEVICE)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def replica_rate(local_units, local_seconds, world):
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time (weak scaling)."""
+    return sum_over_ranks(float(local_units), world) / max_over_ranks(float(local_seconds), world)
 
 
 def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0):
@@ -331,7 +347,7 @@ def main():
     elapsed = start.elapsed_time(end) / 1e3
     elapsed_max = max_over_ranks(elapsed, world)
     total_nnz = sum_over_ranks(float(nnz * args.steps), world)
-    value = total_nnz / elapsed_max
+    value = replica_rate(nnz * args.steps, elapsed, world)
     ms_per_step = elapsed_max / args.steps * 1e3
 
     def avg_ms(key, per_step):

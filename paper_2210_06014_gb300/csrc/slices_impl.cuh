@@ -21,15 +21,24 @@ namespace sft {
 template <int NO>
 struct Sample {
     int32_t i[NO];
+    int32_t row;  // coordinate of mode n (loaded only by walks that need it)
     float x;
     bool ok;
 };
 
 // Coordinates of the other modes and the value at slice-ordered position t
 // (bounds-checked; the slice's own coordinate is known from the layout).
-template <int NO>
+template <int NO, bool WITH_ROW = false>
 __device__ __forceinline__ void load_sample(const PassArgs &a, int64_t t, bool valid, Sample<NO> &c) {
     c.ok = valid;
+    c.row = -1;
+    if constexpr (WITH_ROW) {
+        if (valid) {
+            const int32_t r = __ldg(a.idx[a.n] + t);
+            if ((uint32_t)r < (uint32_t)a.dims[a.n]) c.row = r;
+            else c.ok = false;  // samples with a bad own coordinate sit after the last slice
+        }
+    }
 #pragma unroll
     for (int q = 0; q < NO; ++q) {
         c.i[q] = 0;
@@ -79,35 +88,38 @@ struct WalkDepth {
 // Calls body(x, ok, p) for slice-ordered positions [s0, s1) in order, where p
 // is the lane's 4 entries of prod_{k != n} C^(k)[i_k][:] and ok says whether
 // the position's data was valid.
-template <int NO, int R, int DMAX, typename Body>
+template <int NO, int R, int DMAX, bool WITH_ROW, typename Body>
 __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, int sub,
                                      Body &&body) {
     constexpr int D = WalkDepth<NO, DMAX>::value;
     Rows<NO> ring[D];
     float rx[D];
     bool rok[D];
+    int32_t rrow[D];
     {
         Sample<NO> tmp[D];
 #pragma unroll
-        for (int u = 0; u < D; ++u) load_sample<NO>(a, s0 + u, s0 + u < s1, tmp[u]);
+        for (int u = 0; u < D; ++u) load_sample<NO, WITH_ROW>(a, s0 + u, s0 + u < s1, tmp[u]);
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             load_rows<NO, R>(a, tmp[u], sub, ring[u]);
             rx[u] = tmp[u].x;
             rok[u] = tmp[u].ok;
+            rrow[u] = tmp[u].row;
         }
     }
     Sample<NO> pend;
-    load_sample<NO>(a, s0 + D, s0 + D < s1, pend);
+    load_sample<NO, WITH_ROW>(a, s0 + D, s0 + D < s1, pend);
     for (int64_t t = s0; t < s1; t += D) {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             if (t + u < s1) {
-                body(rx[u], rok[u], product<NO>(ring[u]));
+                body(rrow[u], rx[u], rok[u], product<NO>(ring[u]));
                 load_rows<NO, R>(a, pend, sub, ring[u]);  // position t + u + D
                 rx[u] = pend.x;
                 rok[u] = pend.ok;
-                load_sample<NO>(a, t + u + D + 1, t + u + D + 1 < s1, pend);
+                rrow[u] = pend.row;
+                load_sample<NO, WITH_ROW>(a, t + u + D + 1, t + u + D + 1 < s1, pend);
             }
         }
     }
@@ -140,7 +152,7 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
     float av[JL];
     float *arow = a.A + (int64_t)r * J + sub * JL;
     load_run<JL>(arow, av);
-    walk<NB, R, 4>(a, s0, s1, sub, [&](float x, bool ok, const float4 &p) {
+    walk<NB, R, 4, false>(a, s0, s1, sub, [&](int32_t, float x, bool ok, const float4 &p) {
         float vp[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -185,12 +197,98 @@ __device__ __forceinline__ bool first_boundary_slice(const SliceArgs &g, int64_t
     return s / g.W + 1 == b;
 }
 
+template <int L>
+__device__ __forceinline__ void store_run(float *p, const float (&r)[L]) {
+    if constexpr (L >= 4) {
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q)
+            *reinterpret_cast<float4 *>(p + 4 * q) =
+                make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    } else if constexpr (L == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
+    } else {
+        p[0] = r[0];
+    }
+}
+
 constexpr int kSliceThreads = 256;
 
-// Items [0, ntiles-1): tile boundaries (whole crossing slices of at most Lseq
-// nonzeros); items [ntiles-1, 2 ntiles - 1): tiles (slices inside the tile).
+// Slices inside tiles.  Every lane group walks its tile's positions in order
+// (the same trip count and code path for all groups of a warp), skipping the
+// tile's first run if its slice started before the tile and its last run if
+// its slice continues after it; the factor row is switched in place whenever
+// the slice changes.
 template <int NB, int R, int J>
-__global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_direct(SliceArgs g) {
+__global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles(SliceArgs g) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    __shared__ __align__(16) float sB[J * R];
+    for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
+    __syncthreads();
+    const PassArgs &a = g.a;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const unsigned m = group_mask<T>(lane);
+    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
+    const int32_t *rowidx = a.idx[a.n];
+    const uint32_t In = (uint32_t)a.dims[a.n];
+    for (int64_t t = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T; t < g.ntiles;
+         t += groups) {
+        const int64_t p0 = t * g.W;
+        const int64_t p1 = min(a.nnz, p0 + g.W);
+        int64_t q0 = p0, q1 = p1;
+        bool bad = false;
+        const int32_t r0 = __ldg(rowidx + p0);
+        if (p0 > 0 && (uint32_t)r0 < In && __ldg(rowidx + p0 - 1) == r0) {
+            const int64_t e0 = __ldg(g.row_ptr + r0 + 1);
+            if (e0 <= p0 || e0 > a.nnz) bad = true;
+            else q0 = min(e0, p1);
+        }
+        const int32_t r1 = __ldg(rowidx + p1 - 1);
+        if (p1 < a.nnz && (uint32_t)r1 < In && __ldg(rowidx + p1) == r1) {
+            const int64_t s1 = __ldg(g.row_ptr + r1);
+            if (s1 < 0 || s1 > p1 - 1) bad = true;
+            else q1 = max(s1, q0);
+        }
+        if (bad) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        if (q0 >= q1) continue;
+        int32_t cur = -1;
+        float av[JL];
+#pragma unroll
+        for (int q = 0; q < JL; ++q) av[q] = 0.f;
+        walk<NB, R, 4, true>(a, q0, q1, sub, [&](int32_t row, float x, bool ok, const float4 &p) {
+            if (row != cur) {  // the slice changes: write the finished row, read the next
+                if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
+                cur = row;
+                if (cur >= 0) load_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
+            }
+            float vp[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+                vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
+            }
+            group_reduce_scatter_m<T, J>(vp, sub, m);
+            float dot = 0.f;
+#pragma unroll
+            for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vp[q], dot);
+            const float e = x - group_sum_m<T>(dot, m);
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vp[q] - a.lam * av[q]);
+            }
+        });
+        if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
+    }
+}
+
+// Crossing slices of at most Lseq nonzeros, whole, one per lane group (the
+// group that owns the slice's first tile boundary).
+template <int NB, int R, int J>
+__global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chains(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
@@ -199,36 +297,12 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_direc
     const int sub = lane & (T - 1);
     const unsigned m = group_mask<T>(lane);
     const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
-    const int64_t nb = g.ntiles - 1;
-    const int32_t *rowidx = g.a.idx[g.a.n];
     for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
-         item < nb + g.ntiles; item += groups) {
-        if (item < nb) {
-            int32_t r;
-            int64_t s, e;
-            if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
-                run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
-            continue;
-        }
-        const int64_t t = item - nb;
-        const int64_t p0 = t * g.W;
-        const int64_t p1 = min(g.a.nnz, p0 + g.W);
-        int64_t pos = p0;
-        while (pos < p1) {
-            const int32_t r = __ldg(rowidx + pos);
-            if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) {  // invalid samples sit at the end
-                ++pos;
-                continue;
-            }
-            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
-            if (!slice_ok(g, s, e) || pos < s || pos >= e) {
-                atomicOr(g.a.err, kErrIndex);
-                break;
-            }
-            const int64_t se = min(e, p1);
-            if (s >= p0 && e <= p1) run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
-            pos = se;
-        }
+         item < g.ntiles - 1; item += groups) {
+        int32_t r;
+        int64_t s, e;
+        if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
+            run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
     }
 }
 
@@ -250,7 +324,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 #pragma unroll
         for (int k = 0; k < J; ++k) M[q][k] = (sub * JL + q == k) ? 1.f : 0.f;
     }
-    walk<NB, R, 2>(a, s0, s1, sub, [&](float x0, bool ok0, const float4 &p) {
+    walk<NB, R, 2, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
         float v[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -358,46 +432,16 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
     const int64_t lo = a.base, hi = a.base + a.count;  // minibatch range of positions
     const int64_t ntiles = (a.count + g.W - 1) / g.W;
     const int64_t groups = (int64_t)gridDim.x * GPB;
-    const int32_t *rowidx = a.idx[a.n];
     for (int64_t t = (int64_t)blockIdx.x * GPB + gid; t < ntiles; t += groups) {
         const int64_t p0 = lo + t * g.W;
         const int64_t p1 = min(hi, p0 + g.W);
-        int64_t pos = p0;
-        while (pos < p1) {
-            const int32_t r = __ldg(rowidx + pos);
-            if ((uint32_t)r >= (uint32_t)a.dims[a.n]) {
-                ++pos;
-                continue;
-            }
-            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
-            if (!slice_ok(g, s, e) || pos < s || pos >= e) {
-                atomicOr(a.err, kErrIndex);
-                break;
-            }
-            const int64_t se = min(e, p1);
-            // the whole a row (same addresses across the group) and w = B^T a (lane's 4 r)
-            float arow[J];
-            load_run<J>(a.A + (int64_t)r * J, arow);
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t cur = -1;
+        float arow[J];
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f), qv = w;
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
-                w.x = fmaf(arow[j], b.x, w.x);
-                w.y = fmaf(arow[j], b.y, w.y);
-                w.z = fmaf(arow[j], b.z, w.z);
-                w.w = fmaf(arow[j], b.w, w.w);
-            }
-            float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
-            walk<NB, R, 4>(a, pos, se, sub, [&](float x0, bool ok0, const float4 &p) {
-                const float part = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, w.w * p.w)));
-                const float xh = group_sum_m<T>(part, m);
-                const float ev = ok0 ? x0 - xh : 0.f;
-                qv.x = fmaf(ev, p.x, qv.x);
-                qv.y = fmaf(ev, p.y, qv.y);
-                qv.z = fmaf(ev, p.z, qv.z);
-                qv.w = fmaf(ev, p.w, qv.w);
-            });
-            // G[j][4 sub .. 4 sub + 3] += a_j q  (the lane's four columns of the group tile)
+        for (int j = 0; j < J; ++j) arow[j] = 0.f;
+        // G[j][4 sub .. 4 sub + 3] += a_j q for the finished run (the lane's columns)
+        auto flush = [&]() {
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 float4 *gp = reinterpret_cast<float4 *>(&myG[j * R + 4 * sub]);
@@ -408,8 +452,34 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
                 v.w = fmaf(arow[j], qv.w, v.w);
                 *gp = v;
             }
-            pos = se;
-        }
+        };
+        walk<NB, R, 4, true>(a, p0, p1, sub, [&](int32_t row, float x0, bool ok0, const float4 &p) {
+            if (row != cur) {  // a new run: close the last one, read a and w = B^T a
+                if (cur >= 0) flush();
+                cur = row;
+                qv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (cur >= 0) {
+                    load_run<J>(a.A + (int64_t)cur * J, arow);
+                    w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+                        w.x = fmaf(arow[j], b.x, w.x);
+                        w.y = fmaf(arow[j], b.y, w.y);
+                        w.z = fmaf(arow[j], b.z, w.z);
+                        w.w = fmaf(arow[j], b.w, w.w);
+                    }
+                }
+            }
+            const float part = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, w.w * p.w)));
+            const float xh = group_sum_m<T>(part, m);
+            const float ev = ok0 ? x0 - xh : 0.f;
+            qv.x = fmaf(ev, p.x, qv.x);
+            qv.y = fmaf(ev, p.y, qv.y);
+            qv.z = fmaf(ev, p.z, qv.z);
+            qv.w = fmaf(ev, p.w, qv.w);
+        });
+        if (cur >= 0) flush();
     }
     __syncthreads();
     for (int q = threadIdx.x; q < JR; q += blockDim.x) {
@@ -436,8 +506,13 @@ template <int NB, int R, int J>
 void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
-    const int gd = grid_for(k_slices_direct<NB, R, J>, kSliceThreads, 0, gpb, 2 * g.ntiles - 1, sms);
-    k_slices_direct<NB, R, J><<<gd, kSliceThreads, 0, st>>>(g);
+    if (g.ntiles > 1) {
+        const int gch = grid_for(k_slices_chains<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles - 1, sms);
+        k_slices_chains<NB, R, J><<<gch, kSliceThreads, 0, st>>>(g);
+        *launches += 1;
+    }
+    const int gd = grid_for(k_slices_tiles<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
+    k_slices_tiles<NB, R, J><<<gd, kSliceThreads, 0, st>>>(g);
     *launches += 1;
     if (with_maps && g.ntiles > 1) {
         const int gm = grid_for(k_slices_maps<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
