@@ -10,9 +10,9 @@
 // Minimum resident blocks per SM requested from the register allocator: the
 // slice kernels are latency bound, so occupancy is traded against a few spills
 // for J <= 16; J = 32 keeps more registers.
-#define SFT_DIRECT_MINB (J >= 32 ? 2 : 3)
+#define SFT_DIRECT_MINB 2
 #define SFT_MAPS_MINB (J >= 32 ? 1 : 2)
-#define SFT_CORE_MINB (J >= 32 ? 2 : 5)
+#define SFT_CORE_MINB (J >= 32 ? 2 : 4)
 
 namespace sft {
 
@@ -91,15 +91,22 @@ struct WalkDepth {
 template <int NO, int R, int DMAX, bool WITH_ROW, typename Body>
 __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, int sub,
                                      Body &&body) {
+    // Two-level ring: the cached rows of positions t .. t+D-1 and the
+    // coordinates of positions t+D .. t+2D-1 are in flight, so a row gather is
+    // issued D steps after its coordinates and consumed D steps after that.
     constexpr int D = WalkDepth<NO, DMAX>::value;
     Rows<NO> ring[D];
     float rx[D];
     bool rok[D];
     int32_t rrow[D];
+    Sample<NO> cring[D];
     {
         Sample<NO> tmp[D];
 #pragma unroll
         for (int u = 0; u < D; ++u) load_sample<NO, WITH_ROW>(a, s0 + u, s0 + u < s1, tmp[u]);
+#pragma unroll
+        for (int u = 0; u < D; ++u)
+            load_sample<NO, WITH_ROW>(a, s0 + D + u, s0 + D + u < s1, cring[u]);
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             load_rows<NO, R>(a, tmp[u], sub, ring[u]);
@@ -108,18 +115,16 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
             rrow[u] = tmp[u].row;
         }
     }
-    Sample<NO> pend;
-    load_sample<NO, WITH_ROW>(a, s0 + D, s0 + D < s1, pend);
     for (int64_t t = s0; t < s1; t += D) {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             if (t + u < s1) {
                 body(rrow[u], rx[u], rok[u], product<NO>(ring[u]));
-                load_rows<NO, R>(a, pend, sub, ring[u]);  // position t + u + D
-                rx[u] = pend.x;
-                rok[u] = pend.ok;
-                rrow[u] = pend.row;
-                load_sample<NO, WITH_ROW>(a, t + u + D + 1, t + u + D + 1 < s1, pend);
+                load_rows<NO, R>(a, cring[u], sub, ring[u]);  // position t + u + D
+                rx[u] = cring[u].x;
+                rok[u] = cring[u].ok;
+                rrow[u] = cring[u].row;
+                load_sample<NO, WITH_ROW>(a, t + u + 2 * D, t + u + 2 * D < s1, cring[u]);
             }
         }
     }
