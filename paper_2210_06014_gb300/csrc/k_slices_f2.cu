@@ -3,10 +3,10 @@
 
 namespace sft {
 
-void factor_slices_no2(const SliceArgs &g, int R, int J, bool with_maps, cudaStream_t st,
+void factor_slices_no2(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,
                          int sms, int64_t *launches) {
     dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-        factor_slices_t<2, decltype(r_c)::value, decltype(j_c)::value>(g, with_maps, st, sms,
+        factor_slices_t<2, decltype(r_c)::value, decltype(j_c)::value>(g, with_maps, ss, sms,
                                                                          launches);
     });
 }

@@ -345,8 +345,19 @@ static void dispatch_nb(int N, F &&f) {
 }
 
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, int J, int R, cudaStream_t st, int sms,
+                                 float *maps, int J, int R, const SliceStreams &ss_in, int sms,
                                  int64_t *launches) {
+    SliceStreams ss = ss_in;
+    const cudaStream_t st = ss.tiles;
+    const bool fork = ss.fork && ss.chains_done && ss.maps_done && ss.chains && ss.maps &&
+                      ss.chains != st && ss.maps != st;
+    if (fork) {
+        cudaEventRecord(ss.fork, st);
+        cudaStreamWaitEvent(ss.chains, ss.fork, 0);
+        cudaStreamWaitEvent(ss.maps, ss.fork, 0);
+    } else {
+        ss.chains = ss.maps = st;
+    }
     SliceArgs g{};
     g.a = a;
     g.row_ptr = row_ptr;
@@ -355,10 +366,16 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     const bool with_maps = maps != nullptr;
-    if (a.N <= 3) factor_slices_no2(g, R, J, with_maps, st, sms, launches);
-    else if (a.N <= 4) factor_slices_no3(g, R, J, with_maps, st, sms, launches);
-    else if (a.N <= 8) factor_slices_no7(g, R, J, with_maps, st, sms, launches);
-    else factor_slices_no15(g, R, J, with_maps, st, sms, launches);
+    if (a.N <= 3) factor_slices_no2(g, R, J, with_maps, ss, sms, launches);
+    else if (a.N <= 4) factor_slices_no3(g, R, J, with_maps, ss, sms, launches);
+    else if (a.N <= 8) factor_slices_no7(g, R, J, with_maps, ss, sms, launches);
+    else factor_slices_no15(g, R, J, with_maps, ss, sms, launches);
+    if (fork) {
+        cudaEventRecord(ss.chains_done, ss.chains);
+        cudaEventRecord(ss.maps_done, ss.maps);
+        cudaStreamWaitEvent(st, ss.chains_done, 0);
+        cudaStreamWaitEvent(st, ss.maps_done, 0);
+    }
     if (with_maps && g.ntiles > 1) {
         dispatch_rj(R, J, [&](auto r_c, auto j_c) {
             constexpr int R_ = decltype(r_c)::value, J_ = decltype(j_c)::value;

@@ -36,6 +36,8 @@ struct sft_ctx {
     int64_t det_max_chunks = 0;
     int jmax = 0;
     int64_t launches = 0;
+    cudaStream_t aux[2] = {nullptr, nullptr};  // forked streams of the slice factor pass
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     int64_t slice_tile = 0;        // 0 = automatic
     int64_t slice_max_direct = 0;  // 0 = automatic
     std::string last_error;
@@ -234,6 +236,20 @@ sft_status sft_init(const sft_config *cfg, float *const *A, float *const *B, voi
     if (e != cudaSuccess) {
         delete c;
         return SFT_ECUDA;
+    }
+    // auxiliary streams for the concurrent kernels of a slice factor pass; if
+    // they cannot be created everything runs on the caller's stream
+    bool aux_ok = true;
+    for (int i = 0; i < 2 && aux_ok; ++i)
+        aux_ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 3 && aux_ok; ++i)
+        aux_ok = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!aux_ok) {
+        cudaGetLastError();
+        for (int i = 0; i < 2; ++i) if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+        for (int i = 0; i < 3; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+        c->aux[0] = c->aux[1] = nullptr;
+        c->ev[0] = c->ev[1] = c->ev[2] = nullptr;
     }
     *out = c;
     return SFT_OK;
@@ -472,8 +488,9 @@ sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *co
         return fail(c, SFT_EINVAL, "workspace missing, misaligned or smaller than sft_slices_workspace_bytes");
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
+    SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
     cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, W, nnz), (float *)workspace,
-                                         c->J[mode], c->R, c->stream, c->sms, &c->launches);
+                                         c->J[mode], c->R, ss, c->sms, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
     return SFT_OK;
 }
@@ -534,6 +551,11 @@ const char *sft_last_error(const sft_ctx *c) { return c ? c->last_error.c_str() 
 
 int64_t sft_launch_count(const sft_ctx *c) { return c ? c->launches : 0; }
 
-void sft_destroy(sft_ctx *c) { delete c; }
+void sft_destroy(sft_ctx *c) {
+    if (!c) return;
+    for (int i = 0; i < 2; ++i) if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+    for (int i = 0; i < 3; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    delete c;
+}
 
 }  // extern "C"

@@ -61,6 +61,12 @@ cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nb
 int core_blocks_for(int64_t count, int sms);
 cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
                               float lr, float lam, cudaStream_t st);
+// Streams of one slice factor pass: `tiles` is the caller's stream; `chains`
+// and `maps` may be auxiliary streams forked from it (or the same stream).
+struct SliceStreams {
+    cudaStream_t tiles, chains, maps;
+    cudaEvent_t fork, chains_done, maps_done;  // NULL events: no fork/join
+};
 // slice (CSF) layout and the passes over it
 int64_t slice_sort_length(int64_t nnz);
 int slice_tile_length(int64_t nnz, int sms);
@@ -68,7 +74,7 @@ cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, floa
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches);
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, int J, int R, cudaStream_t st, int sms,
+                                 float *maps, int J, int R, const SliceStreams &ss, int sms,
                                  int64_t *launches);
 cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
                                float *partials, int max_blocks, cudaStream_t st, int sms,

@@ -321,7 +321,16 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     constexpr int T = R / 4;
     constexpr int JL = J / T;
     const PassArgs &a = g.a;
+    // The map is kept as M = alpha^n M', c = alpha^n c' (n = steps since the
+    // last fold), so one step is a pure rank-1 FFMA update:
+    //   M' <- M' - (lr/alpha) v (v^T M'),
+    //   c' <- c' - (lr/alpha) v (v^T c') + lr x alpha^-(n+1) v;
+    // the factor alpha^n is folded back in every 16 steps and at the end.
     const float alpha = 1.f - a.lr * a.lam;
+    const float ainv = 1.f / alpha;
+    const float nvc = -a.lr * ainv;
+    float apow = 1.f, pw = ainv;
+    int since = 0;
     float M[JL][J], cv[JL];
 #pragma unroll
     for (int q = 0; q < JL; ++q) {
@@ -329,6 +338,17 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 #pragma unroll
         for (int k = 0; k < J; ++k) M[q][k] = (sub * JL + q == k) ? 1.f : 0.f;
     }
+    auto fold = [&]() {
+#pragma unroll
+        for (int q = 0; q < JL; ++q) {
+#pragma unroll
+            for (int k = 0; k < J; ++k) M[q][k] *= apow;
+            cv[q] *= apow;
+        }
+        apow = 1.f;
+        pw = ainv;
+        since = 0;
+    };
     walk<NB, R, 2, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
         float v[J];
 #pragma unroll
@@ -337,7 +357,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
             v[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
         }
         group_reduce_scatter_m<T, J>(v, sub, m);  // v[0..JL): the lane's slice of v
-        // w = v^T M (all J columns), s = v . c
+        // w = v^T M' (all J columns), s = v . c'
         float w[J];
 #pragma unroll
         for (int k = 0; k < J; ++k) {
@@ -353,15 +373,20 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         for (int k = 0; k < J; ++k) w[k] = group_sum_m<T>(w[k], m);
         sc = group_sum_m<T>(sc, m);
         if (ok0) {
+            const float xs = a.lr * x0 * pw;
 #pragma unroll
             for (int q = 0; q < JL; ++q) {
-                const float lv = a.lr * v[q];
+                const float nv = nvc * v[q];
 #pragma unroll
-                for (int k = 0; k < J; ++k) M[q][k] = fmaf(alpha, M[q][k], -lv * w[k]);
-                cv[q] = fmaf(alpha, cv[q], lv * (x0 - sc));
+                for (int k = 0; k < J; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
+                cv[q] = fmaf(xs, v[q], fmaf(nv, sc, cv[q]));
             }
+            apow *= alpha;
+            pw *= ainv;
+            if (++since == 16) fold();
         }
     });
+    fold();
 #pragma unroll
     for (int q = 0; q < JL; ++q) {
 #pragma unroll
@@ -507,21 +532,24 @@ inline int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block,
     return (int)b;
 }
 
+// The three kernels touch disjoint data (chains and tiles write different
+// factor rows, maps write only the map workspace), so they may run on three
+// streams at once.
 template <int NB, int R, int J>
-void factor_slices_t(const SliceArgs &g, bool with_maps, cudaStream_t st, int sms,
+void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
     if (g.ntiles > 1) {
         const int gch = grid_for(k_slices_chains<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles - 1, sms);
-        k_slices_chains<NB, R, J><<<gch, kSliceThreads, 0, st>>>(g);
+        k_slices_chains<NB, R, J><<<gch, kSliceThreads, 0, ss.chains>>>(g);
         *launches += 1;
     }
     const int gd = grid_for(k_slices_tiles<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
-    k_slices_tiles<NB, R, J><<<gd, kSliceThreads, 0, st>>>(g);
+    k_slices_tiles<NB, R, J><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
     *launches += 1;
     if (with_maps && g.ntiles > 1) {
         const int gm = grid_for(k_slices_maps<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
-        k_slices_maps<NB, R, J><<<gm, kSliceThreads, 0, st>>>(g);
+        k_slices_maps<NB, R, J><<<gm, kSliceThreads, 0, ss.maps>>>(g);
         *launches += 1;
     }
 }
@@ -544,7 +572,7 @@ int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStrea
 // Per-order wrappers (defined in k_slices_f<NO>.cu / k_slices_c<NO>.cu).
 #define SFT_SLICE_WRAPPERS(NO)                                                              \
     void factor_slices_no##NO(const SliceArgs &g, int R, int J, bool with_maps,            \
-                              cudaStream_t st, int sms, int64_t *launches);                 \
+                              const SliceStreams &ss, int sms, int64_t *launches);          \
     int core_slices_no##NO(const SliceArgs &g, int R, int J, float *partials, int max_blocks, \
                            cudaStream_t st, int sms);
 SFT_SLICE_WRAPPERS(2)
