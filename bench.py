@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--path", default="slices", choices=["slices", "coo"])
+    p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
+    p.add_argument("--slice-max-direct", type=int, default=0,
+                   help="longest crossing slice run element by element (0 = automatic)")
     return p.parse_args()
 
 
@@ -267,6 +270,7 @@ def main():
     layout_s = 0.0
     rows_per_nnz = 1.0
     if args.path == "slices":
+        dec.set_slice_tiling(args.slice_tile, args.slice_max_direct)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         slices = [dec.slices(n, idx, val, None) for n in range(N)]
