@@ -18,41 +18,24 @@ namespace sft {
 
 // ============================================================================ shared pieces
 // NO = number of "other" mode slots (modes != n), a compile-time bound on N-1.
+// A Sample holds the raw loads of one position; nothing consumes them until
+// the position's cached rows are gathered D steps later, so issuing the loads
+// never waits on memory.
 template <int NO>
 struct Sample {
     int32_t i[NO];
     int32_t row;  // coordinate of mode n (loaded only by walks that need it)
     float x;
-    bool ok;
+    bool valid;   // the position exists (a property of the range, not of the data)
 };
 
-// Coordinates of the other modes and the value at slice-ordered position t
-// (bounds-checked; the slice's own coordinate is known from the layout).
 template <int NO, bool WITH_ROW = false>
 __device__ __forceinline__ void load_sample(const PassArgs &a, int64_t t, bool valid, Sample<NO> &c) {
-    c.ok = valid;
-    c.row = -1;
-    if constexpr (WITH_ROW) {
-        if (valid) {
-            const int32_t r = __ldg(a.idx[a.n] + t);
-            if ((uint32_t)r < (uint32_t)a.dims[a.n]) c.row = r;
-            else c.ok = false;  // samples with a bad own coordinate sit after the last slice
-        }
-    }
+    c.valid = valid;
 #pragma unroll
-    for (int q = 0; q < NO; ++q) {
-        c.i[q] = 0;
-        if (c.ok && q < a.N - 1) {
-            const int32_t v = __ldg(a.oidx[q] + t);
-            if ((uint32_t)v >= (uint32_t)a.odims[q]) {
-                atomicOr(a.err, kErrIndex);
-                c.ok = false;
-            } else {
-                c.i[q] = v;
-            }
-        }
-    }
-    c.x = c.ok ? __ldg(a.val + t) : 0.f;
+    for (int q = 0; q < NO; ++q) c.i[q] = (valid && q < a.N - 1) ? __ldg(a.oidx[q] + t) : 0;
+    c.row = (WITH_ROW && valid) ? __ldg(a.idx[a.n] + t) : -1;
+    c.x = valid ? __ldg(a.val + t) : 0.f;
 }
 
 template <int NO>
@@ -60,13 +43,26 @@ struct Rows {
     float4 r[NO];
 };
 
-template <int NO, int R>
+// Checks the coordinates of a sample (they have arrived by now), reports bad
+// data, and gathers the lane's float4 of every other mode's cached row.
+template <int NO, int R, bool WITH_ROW = false>
 __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c, int sub,
-                                          Rows<NO> &w) {
+                                          Rows<NO> &w, bool &ok, int32_t &row) {
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (c.ok && q < a.N - 1) ? ldg4(a.oC[q] + (int64_t)c.i[q] * R + 4 * sub)
-                                       : make_float4(1.f, 1.f, 1.f, 1.f);
+        if (q < a.N - 1) bad |= (uint32_t)c.i[q] >= (uint32_t)a.odims[q];
+    row = c.row;
+    if (WITH_ROW && (uint32_t)row >= (uint32_t)a.dims[a.n]) {
+        bad = true;  // samples with a bad own coordinate sit after the last slice
+        row = -1;
+    }
+    if (c.valid && bad) atomicOr(a.err, kErrIndex);
+    ok = c.valid && !bad;
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+        w.r[q] = (ok && q < a.N - 1) ? ldg4(a.oC[q] + (int64_t)c.i[q] * R + 4 * sub)
+                                     : make_float4(1.f, 1.f, 1.f, 1.f);
 }
 
 template <int NO>
@@ -91,8 +87,8 @@ struct WalkDepth {
 template <int NO, int R, int DMAX, bool WITH_ROW, typename Body>
 __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, int sub,
                                      Body &&body) {
-    // Two-level ring: the cached rows of positions t .. t+D-1 and the
-    // coordinates of positions t+D .. t+2D-1 are in flight, so a row gather is
+    // Two-level ring: the cached rows of positions t .. t+D-1 and the raw
+    // coordinates of positions t+D .. t+2D-1 are in flight; a row gather is
     // issued D steps after its coordinates and consumed D steps after that.
     constexpr int D = WalkDepth<NO, DMAX>::value;
     Rows<NO> ring[D];
@@ -109,10 +105,8 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
             load_sample<NO, WITH_ROW>(a, s0 + D + u, s0 + D + u < s1, cring[u]);
 #pragma unroll
         for (int u = 0; u < D; ++u) {
-            load_rows<NO, R>(a, tmp[u], sub, ring[u]);
+            load_rows<NO, R, WITH_ROW>(a, tmp[u], sub, ring[u], rok[u], rrow[u]);
             rx[u] = tmp[u].x;
-            rok[u] = tmp[u].ok;
-            rrow[u] = tmp[u].row;
         }
     }
     for (int64_t t = s0; t < s1; t += D) {
@@ -120,10 +114,9 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
         for (int u = 0; u < D; ++u) {
             if (t + u < s1) {
                 body(rrow[u], rx[u], rok[u], product<NO>(ring[u]));
-                load_rows<NO, R>(a, cring[u], sub, ring[u]);  // position t + u + D
+                // position t + u + D: its coordinates arrived D steps ago
+                load_rows<NO, R, WITH_ROW>(a, cring[u], sub, ring[u], rok[u], rrow[u]);
                 rx[u] = cring[u].x;
-                rok[u] = cring[u].ok;
-                rrow[u] = cring[u].row;
                 load_sample<NO, WITH_ROW>(a, t + u + 2 * D, t + u + 2 * D < s1, cring[u]);
             }
         }
