@@ -213,6 +213,11 @@ __device__ __forceinline__ bool long_piece(const SliceArgs &g, int64_t t, int si
 
 constexpr int kComposeGroups = 8;  // lane groups per block of k_slices_compose
 
+// X (the running block map, rows of X.M then X.c) lives in shared memory; lane
+// `sub` owns columns [sub*JL, (sub+1)*JL) of X.M and rows [sub*JL, ...) of X.c.
+// Each product X <- X o P first pulls the lane's column slice of P.M and all of
+// P.c into registers (one memory latency per product), then computes the new
+// columns from the whole of X; a group barrier separates reads from writes.
 template <int R, int J>
 __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(SliceArgs g) {
     constexpr int T = R / 4;
@@ -221,7 +226,8 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
     __shared__ __align__(16) float sX[kComposeGroups * MS];
     const int sub = threadIdx.x & (T - 1);
     const int gid = threadIdx.x / T;
-    float *X = sX + gid * MS;  // rows of X.M, then X.c; lane `sub` touches only its rows
+    const unsigned m = group_mask<T>(threadIdx.x & 31);
+    float *X = sX + gid * MS;
     const int64_t groups = (int64_t)gridDim.x * kComposeGroups;
     for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
         for (int side = 0; side < 2; ++side) {
@@ -234,44 +240,60 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
             const int64_t tl = min(t + Bc - 1, t1);
             if (tl == t) continue;  // a block of one piece is already its own map
             const float *P = g.maps + (tl * 2 + piece_slot(s, tl, g.W)) * (int64_t)MS;
-            for (int q = 0; q < JL; ++q) {
-                const int j = sub * JL + q;
-                for (int k = 0; k < J; ++k) X[j * J + k] = __ldg(P + j * J + k);
-                X[J * J + j] = __ldg(P + J * J + j);
-            }
+            for (int j = 0; j < J; ++j)
+#pragma unroll
+                for (int q = 0; q < JL; ++q) X[j * J + sub * JL + q] = __ldcg(P + j * J + sub * JL + q);
+#pragma unroll
+            for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = __ldcg(P + J * J + sub * JL + q);
+            __syncwarp(m);
             for (int64_t u = tl - 1; u >= t; --u) {
                 P = g.maps + (u * 2 + piece_slot(s, u, g.W)) * (int64_t)MS;
+                float pc[J];          // all of P.c
+                float pm[J][JL];      // the lane's columns of P.M
+#pragma unroll
+                for (int l = 0; l < J; ++l) {
+                    pc[l] = __ldcg(P + J * J + l);
+#pragma unroll
+                    for (int q = 0; q < JL; ++q) pm[l][q] = __ldcg(P + l * J + sub * JL + q);
+                }
+                // new X.c for the lane's rows (reads rows of the old X.M)
+                float nc[JL];
+#pragma unroll
                 for (int q = 0; q < JL; ++q) {
                     const int j = sub * JL + q;
-                    // new row j of X.M P.M and new X.c[j] = X.M[j] . P.c + X.c[j]
-                    float nr[J];
+                    float acc = X[J * J + j];
 #pragma unroll
-                    for (int k = 0; k < J; ++k) nr[k] = 0.f;
-                    float nc = X[J * J + j];
-#pragma unroll 4
-                    for (int l = 0; l < J; ++l) {
-                        const float xl = X[j * J + l];
-                        nc = fmaf(xl, __ldg(P + J * J + l), nc);
-#pragma unroll
-                        for (int k4 = 0; k4 < J / 4; ++k4) {
-                            const float4 v = __ldg(reinterpret_cast<const float4 *>(P + l * J) + k4);
-                            nr[4 * k4] = fmaf(xl, v.x, nr[4 * k4]);
-                            nr[4 * k4 + 1] = fmaf(xl, v.y, nr[4 * k4 + 1]);
-                            nr[4 * k4 + 2] = fmaf(xl, v.z, nr[4 * k4 + 2]);
-                            nr[4 * k4 + 3] = fmaf(xl, v.w, nr[4 * k4 + 3]);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < J; ++k) X[j * J + k] = nr[k];
-                    X[J * J + j] = nc;
+                    for (int l = 0; l < J; ++l) acc = fmaf(X[j * J + l], pc[l], acc);
+                    nc[q] = acc;
                 }
+                // one row of X.M at a time: read it whole, then write the lane's columns
+#pragma unroll 1
+                for (int j = 0; j < J; ++j) {
+                    float nrow[JL];
+#pragma unroll
+                    for (int q = 0; q < JL; ++q) nrow[q] = 0.f;
+#pragma unroll
+                    for (int l = 0; l < J; ++l) {
+                        const float xjl = X[j * J + l];
+#pragma unroll
+                        for (int q = 0; q < JL; ++q) nrow[q] = fmaf(xjl, pm[l][q], nrow[q]);
+                    }
+                    __syncwarp(m);
+#pragma unroll
+                    for (int q = 0; q < JL; ++q) X[j * J + sub * JL + q] = nrow[q];
+                    __syncwarp(m);
+                }
+#pragma unroll
+                for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = nc[q];
+                __syncwarp(m);
             }
             float *out = g.maps + (t * 2 + piece_slot(s, t, g.W)) * (int64_t)MS;
-            for (int q = 0; q < JL; ++q) {
-                const int j = sub * JL + q;
-                for (int k = 0; k < J; ++k) out[j * J + k] = X[j * J + k];
-                out[J * J + j] = X[J * J + j];
-            }
+            for (int j = 0; j < J; ++j)
+#pragma unroll
+                for (int q = 0; q < JL; ++q) out[j * J + sub * JL + q] = X[j * J + sub * JL + q];
+#pragma unroll
+            for (int q = 0; q < JL; ++q) out[J * J + sub * JL + q] = X[J * J + sub * JL + q];
+            __syncwarp(m);
         }
     }
 }
