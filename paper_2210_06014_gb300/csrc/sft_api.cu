@@ -417,18 +417,15 @@ static int64_t slice_W(const sft_ctx *c, int64_t nnz) {
     return c->slice_tile > 0 ? c->slice_tile : slice_tile_length(nnz, c->sms);
 }
 
-// Longest crossing slice run as one element-by-element chain: about a third of
-// the pass's streaming time (bytes at ~6.8 TB/s) at ~0.4 us per dependent step,
-// so chains stay off the critical path; longer slices are split into maps.
+// Longest crossing slice run as one element-by-element chain.  A chain step
+// is a dependent sequence of shuffles and FMAs (a few hundred cycles), so
+// chains much longer than a couple of tiles become the pass's tail; measured
+// on the ratings workload, 2 tiles beat both longer chains and maps only.
 static int64_t slice_Lseq(const sft_ctx *c, int64_t W, int64_t nnz) {
+    (void)nnz;
     if (c->slice_max_direct > 0) return c->slice_max_direct;
     if (c->slice_max_direct < 0) return 0;
-    const double bytes = (double)nnz * (4.0 * c->N + 4.0 + 4.0 * (c->N - 1) * c->R);
-    const double pass_us = bytes / 6.8e6;
-    int64_t L = (int64_t)(pass_us / 3.0 / 0.4);
-    if (L < 2 * W) L = 2 * W;
-    if (L > (1 << 20)) L = 1 << 20;
-    return L;
+    return 2 * W;
 }
 
 size_t sft_slices_scratch_bytes(int64_t nnz) {
