@@ -52,6 +52,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--path", default="slices", choices=["slices", "coo"])
+    p.add_argument("--prec", default="fp32", choices=["fp32", "bf16"],
+                   help="storage of the cached products C (arithmetic is float32 either way)")
+    p.add_argument("--workload", default="ratings", choices=["ratings", "order8"],
+                   help="ratings: 480000x17800x2200, 100M nnz, J=R=16; order8: 8 modes of "
+                        "10000, 50M nnz, J=R=32")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
     p.add_argument("--slice-max-direct", type=int, default=0,
                    help="longest crossing slice run element by element (0 = automatic)")
@@ -181,14 +186,14 @@ def replica_rate(local_units, local_seconds, world):
     return sum_over_ranks(float(local_units), world) / max_over_ranks(float(local_seconds), world)
 
 
-def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0):
-    """Bytes per nonzero of one factor / core pass (float32): the COO entry,
-    the N-1 gathered C rows, and the factor row (read + write for the factor
-    pass, read for the core pass).  On the slice layout a factor row is read
-    and written once per slice instead of once per nonzero, so its bytes are
-    scaled by rows_per_nnz = (touched rows) / nnz."""
+def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0, c_bytes=4):
+    """Bytes per nonzero of one factor / core pass: the COO entry, the N-1
+    gathered C rows (c_bytes per entry: 4 float32, 2 bfloat16), and the float32
+    factor row (read + write for the factor pass, read for the core pass).  On
+    the slice layout a factor row is read and written once per slice instead of
+    once per nonzero, so its bytes are scaled by rows_per_nnz = rows / nnz."""
     coo = 4 * N + 4
-    gather = (N - 1) * R * 4
+    gather = (N - 1) * R * c_bytes
     f = rows_per_nnz if path == "slices" else 1.0
     return coo + gather + 2 * J * 4 * f, coo + gather + J * 4 * f
 
@@ -221,7 +226,11 @@ def main():
     world, rank, local = dist_setup(args)
     from paper_2210_06014_gb300 import synth
 
-    spec = synth.spec_ratings(nnz=args.nnz)
+    if args.workload == "order8":
+        spec = synth.spec_order(8, 10_000, args.nnz if args.nnz != 100_000_000 else 50_000_000, 32)
+        spec.test_fraction = 0.1
+    else:
+        spec = synth.spec_ratings(nnz=args.nnz)
     workload = spec.name
     N, J, R = spec.order, spec.J[0], spec.R
     metric = "SGD nonzeros/s (factor+core updates)"
@@ -264,7 +273,8 @@ def main():
     nnz, ntest = T.nnz, int(tval.numel())
     core_batch = args.core_batch if args.core_batch > 0 else nnz
     stream = torch.cuda.current_stream()
-    dec = sft.Decomposition(T.A0, T.B0, deterministic=False, max_batch=4096)
+    prec = sft.SFT_BF16 if args.prec == "bf16" else sft.SFT_FP32
+    dec = sft.Decomposition(T.A0, T.B0, deterministic=False, max_batch=4096, prec=prec)
     loss_out = torch.zeros(2, dtype=torch.float64, device=dev)
     slices = []
     layout_s = 0.0
@@ -362,7 +372,8 @@ def main():
     c_ms, c_step = avg_ms("core", N)
     r_ms, r_step = avg_ms("refresh", 2 * N)
     l_ms, l_step = avg_ms("loss", 1)
-    fac_bytes, core_bytes = algorithmic_bytes(N, J, R, args.path, rows_per_nnz)
+    fac_bytes, core_bytes = algorithmic_bytes(N, J, R, args.path, rows_per_nnz,
+                                              2 if args.prec == "bf16" else 4)
     peak, peak_kind = peaks()
     kernels = {
         "factor": (f_ms, fac_bytes * nnz / (f_ms / 1e3) / 1e9),
@@ -371,7 +382,7 @@ def main():
     dom = "factor" if f_step >= c_step else "core"
     ach = kernels[dom][1]
     sse, sae = loss_out.tolist()
-    test_rmse = (sse / ntest) ** 0.5
+    test_rmse = (sse / ntest) ** 0.5 if ntest else None
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -410,6 +421,7 @@ def main():
             "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "c_storage": args.prec,
             "config": {
                 "workload": workload, "train_nnz": nnz, "test_nnz": ntest, "J": J, "R": R,
                 "parallelism": "replicas only" if world > 1 else "single GPU",

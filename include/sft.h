@@ -19,8 +19,9 @@
  *
  * Memory: every array is a *device* pointer owned by the caller (e.g. torch
  * tensors); the library borrows them and frees nothing it did not allocate.
- * Matrices are dense row-major float32, 16-byte aligned, with no padding:
- * A[n] has I_n*J_n elements, B[n] J_n*R, C[n] I_n*R.  A COO set is given as
+ * Matrices are dense row-major, 16-byte aligned, with no padding: A[n] has
+ * I_n*J_n float32, B[n] J_n*R float32, C[n] I_n*R float32 (bfloat16 with
+ * SFT_BF16).  A COO set is given as
  * N device pointers idx[k] (int32, nnz entries each, 0 <= idx[k][s] < I_k) and
  * val (float32, nnz entries).  An optional permutation perm (uint32, nnz
  * entries, a permutation of 0..nnz-1) gives the order in which the nonzeros
@@ -63,7 +64,10 @@ typedef enum {
 
 typedef enum {
     SFT_FP32 = 0, /* A, B, C float32 */
-    SFT_BF16 = 1  /* reserved: C and a shadow of A in bfloat16 (not yet supported) */
+    SFT_BF16 = 1  /* C stored as bfloat16 (rounded to nearest even by sft_refresh_C);
+                     A and B stay float32 and all arithmetic is float32.  Supported by
+                     the slice calls, sft_refresh_C, sft_loss and sft_predict; the COO
+                     update calls return SFT_ENOTSUP. */
 } sft_precision;
 
 typedef struct {
@@ -83,7 +87,8 @@ typedef struct {
 size_t sft_workspace_bytes(const sft_config *cfg, int64_t max_batch);
 
 /* Create a context.  A, B, C: host arrays of N device pointers (see header
- * comment for layout).  A_lo must be NULL (reserved for the bf16 shadow).
+ * comment for layout).  A_lo must be NULL (reserved; the bfloat16 form keeps
+ * no copy of A).
  * workspace: device buffer of at least sft_workspace_bytes(cfg, max_batch)
  * bytes, 256-byte aligned, owned by the caller and not touched by anyone else
  * while the context lives.  The context copies cfg and the pointer arrays.

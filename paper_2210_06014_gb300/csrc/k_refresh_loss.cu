@@ -15,7 +15,7 @@ namespace sft {
 // T = R/4 lanes per row of C; lane `sub` produces C[i][4 sub .. 4 sub + 3]
 // from the whole a row (same addresses across the T lanes) and B^(n) staged in
 // shared memory.  Grid-stride over rows; stores are float4 and coalesced.
-template <int R, int J>
+template <int R, int J, typename CT>
 __global__ void __launch_bounds__(256) k_refresh(const float *__restrict__ A,
                                                  const float *__restrict__ B,
                                                  float *__restrict__ C, int64_t I) {
@@ -42,19 +42,22 @@ __global__ void __launch_bounds__(256) k_refresh(const float *__restrict__ A,
             c.z = fmaf(a[j], b.z, c.z);
             c.w = fmaf(a[j], b.w, c.w);
         }
-        *reinterpret_cast<float4 *>(C + row * R + 4 * sub) = c;
+        stC<CT>(C, row * R + 4 * sub, c);
     }
 }
 
 cudaError_t launch_refresh(const float *A, const float *B, float *C, int64_t I, int J, int R,
-                           cudaStream_t st, int sms) {
+                           bool cbf16, cudaStream_t st, int sms) {
     const int threads = 256;
     const int64_t rows_per_block = threads / (R / 4);
     int64_t blocks = (I + rows_per_block - 1) / rows_per_block;
     const int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    SFT_DISPATCH_RJ(R, J, (k_refresh<R_, J_><<<(int)blocks, threads, 0, st>>>(A, B, C, I)));
+    if (cbf16)
+        SFT_DISPATCH_RJ(R, J, (k_refresh<R_, J_, __nv_bfloat16><<<(int)blocks, threads, 0, st>>>(A, B, C, I)));
+    else
+        SFT_DISPATCH_RJ(R, J, (k_refresh<R_, J_, float><<<(int)blocks, threads, 0, st>>>(A, B, C, I)));
     return cudaGetLastError();
 }
 
@@ -65,7 +68,7 @@ cudaError_t launch_refresh(const float *A, const float *B, float *C, int64_t I, 
 // the result is bitwise reproducible for a given grid size.
 constexpr int kLossThreads = 256;
 
-template <int R>
+template <int R, typename CT>
 __global__ void __launch_bounds__(kLossThreads) k_loss(PassArgs a, double *__restrict__ partials) {
     constexpr int T = R / 4;
     constexpr int GPW = 32 / T;
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(PassArgs a, double *__res
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = k0 + u;
-                    c[u] = (ok && k < a.N) ? ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub)
+                    c[u] = (ok && k < a.N) ? ldC<CT>(a.C[k], (int64_t)ik[k] * R + 4 * sub)
                                            : make_float4(1.f, 1.f, 1.f, 1.f);
                 }
 #pragma unroll
@@ -168,7 +171,10 @@ int loss_blocks_for(int64_t count, int sms) {
 
 cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, double *out2,
                         cudaStream_t st) {
-    SFT_DISPATCH_R(R, (k_loss<R_><<<nblk, kLossThreads, 0, st>>>(a, partials)));
+    if (a.cbf16)
+        SFT_DISPATCH_R(R, (k_loss<R_, __nv_bfloat16><<<nblk, kLossThreads, 0, st>>>(a, partials)));
+    else
+        SFT_DISPATCH_R(R, (k_loss<R_, float><<<nblk, kLossThreads, 0, st>>>(a, partials)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_loss_final<<<1, 32, 0, st>>>(partials, nblk, out2);
@@ -176,7 +182,7 @@ cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, do
 }
 
 // --------------------------------------------------------------------------- predict
-template <int R>
+template <int R, typename CT>
 __global__ void __launch_bounds__(kLossThreads) k_predict(PassArgs a, float *__restrict__ out) {
     constexpr int T = R / 4;
     constexpr int GPW = 32 / T;
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(kLossThreads) k_predict(PassArgs a, float *__r
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = k0 + u;
-                    c[u] = (ok && k < a.N) ? ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub)
+                    c[u] = (ok && k < a.N) ? ldC<CT>(a.C[k], (int64_t)ik[k] * R + 4 * sub)
                                            : make_float4(1.f, 1.f, 1.f, 1.f);
                 }
 #pragma unroll
@@ -225,7 +231,10 @@ cudaError_t launch_predict(const PassArgs &a, int R, float *out, cudaStream_t st
     const int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    SFT_DISPATCH_R(R, (k_predict<R_><<<(int)blocks, kLossThreads, 0, st>>>(a, out)));
+    if (a.cbf16)
+        SFT_DISPATCH_R(R, (k_predict<R_, __nv_bfloat16><<<(int)blocks, kLossThreads, 0, st>>>(a, out)));
+    else
+        SFT_DISPATCH_R(R, (k_predict<R_, float><<<(int)blocks, kLossThreads, 0, st>>>(a, out)));
     return cudaGetLastError();
 }
 

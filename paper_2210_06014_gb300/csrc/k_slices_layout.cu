@@ -388,10 +388,17 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     const bool with_maps = maps != nullptr;
-    if (a.N <= 3) factor_slices_no2(g, R, J, with_maps, ss, sms, launches);
-    else if (a.N <= 4) factor_slices_no3(g, R, J, with_maps, ss, sms, launches);
-    else if (a.N <= 8) factor_slices_no7(g, R, J, with_maps, ss, sms, launches);
-    else factor_slices_no15(g, R, J, with_maps, ss, sms, launches);
+    if (a.cbf16) {
+        if (a.N <= 3) factor_slices_no2_bf16(g, R, J, with_maps, ss, sms, launches);
+        else if (a.N <= 4) factor_slices_no3_bf16(g, R, J, with_maps, ss, sms, launches);
+        else if (a.N <= 8) factor_slices_no7_bf16(g, R, J, with_maps, ss, sms, launches);
+        else factor_slices_no15_bf16(g, R, J, with_maps, ss, sms, launches);
+    } else {
+        if (a.N <= 3) factor_slices_no2_f32(g, R, J, with_maps, ss, sms, launches);
+        else if (a.N <= 4) factor_slices_no3_f32(g, R, J, with_maps, ss, sms, launches);
+        else if (a.N <= 8) factor_slices_no7_f32(g, R, J, with_maps, ss, sms, launches);
+        else factor_slices_no15_f32(g, R, J, with_maps, ss, sms, launches);
+    }
     if (fork) {
         cudaEventRecord(ss.chains_done, ss.chains);
         cudaEventRecord(ss.maps_done, ss.maps);
@@ -424,10 +431,17 @@ cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_
     g.ntiles = (a.count + W - 1) / W;
     g.maps = nullptr;
     int nblk;
-    if (a.N <= 3) nblk = core_slices_no2(g, R, J, partials, max_blocks, st, sms);
-    else if (a.N <= 4) nblk = core_slices_no3(g, R, J, partials, max_blocks, st, sms);
-    else if (a.N <= 8) nblk = core_slices_no7(g, R, J, partials, max_blocks, st, sms);
-    else nblk = core_slices_no15(g, R, J, partials, max_blocks, st, sms);
+    if (a.cbf16) {
+        if (a.N <= 3) nblk = core_slices_no2_bf16(g, R, J, partials, max_blocks, st, sms);
+        else if (a.N <= 4) nblk = core_slices_no3_bf16(g, R, J, partials, max_blocks, st, sms);
+        else if (a.N <= 8) nblk = core_slices_no7_bf16(g, R, J, partials, max_blocks, st, sms);
+        else nblk = core_slices_no15_bf16(g, R, J, partials, max_blocks, st, sms);
+    } else {
+        if (a.N <= 3) nblk = core_slices_no2_f32(g, R, J, partials, max_blocks, st, sms);
+        else if (a.N <= 4) nblk = core_slices_no3_f32(g, R, J, partials, max_blocks, st, sms);
+        else if (a.N <= 8) nblk = core_slices_no7_f32(g, R, J, partials, max_blocks, st, sms);
+        else nblk = core_slices_no15_f32(g, R, J, partials, max_blocks, st, sms);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches += 2;

@@ -17,6 +17,7 @@ struct sft_ctx {
     int N = 0;
     int R = 0;
     int deterministic = 0;
+    int cbf16 = 0;  // cached products stored as bfloat16 (SFT_BF16)
     int64_t dims[kMaxOrder] = {};
     int32_t J[kMaxOrder] = {};
     float *A[kMaxOrder] = {};
@@ -99,7 +100,6 @@ const char *check_config(const sft_config *cfg, sft_status *st) {
     }
     if (cfg->prec != SFT_FP32 && cfg->prec != SFT_BF16) return "unknown precision";
     *st = SFT_ENOTSUP;
-    if (cfg->prec != SFT_FP32) return "only SFT_FP32 is supported by this build";
     if (!supported_rank(cfg->R)) return "R must be one of 4, 8, 16, 32";
     for (int n = 0; n < cfg->order; ++n) {
         if (!supported_rank(cfg->J[n])) return "each J_n must be one of 4, 8, 16, 32";
@@ -160,6 +160,7 @@ PassArgs pass_args(const sft_ctx *c, int mode, const int32_t *const *idx, const 
     a.lr = lr;
     a.lam = lam;
     a.err = c->err;
+    a.cbf16 = c->cbf16;
     return a;
 }
 
@@ -201,6 +202,7 @@ sft_status sft_init(const sft_config *cfg, float *const *A, float *const *B, voi
     c->N = cfg->order;
     c->R = cfg->R;
     c->deterministic = cfg->deterministic ? 1 : 0;
+    c->cbf16 = cfg->prec == SFT_BF16 ? 1 : 0;
     c->stream = (cudaStream_t)cfg->stream;
     c->device = device;
     c->sms = sms;
@@ -261,7 +263,7 @@ sft_status sft_refresh_C(sft_ctx *c, int32_t mode) {
     for (int n = 0; n < c->N; ++n) {
         if (mode >= 0 && n != mode) continue;
         cudaError_t e = launch_refresh(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R,
-                                       c->stream, c->sms);
+                                       c->cbf16 != 0, c->stream, c->sms);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(c, e, "refresh launch");
     }
@@ -276,6 +278,9 @@ sft_status sft_update_factors(sft_ctx *c, int32_t mode, const int32_t *const *id
     sft_status st = check_set(c, idx, val, nnz);
     if (st != SFT_OK) return st;
     if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (c->cbf16)
+        return fail(c, SFT_ENOTSUP, "the COO factor pass needs float32 cached products; use the "
+                                    "slice calls with SFT_BF16");
     if (nnz == 0) return SFT_OK;
     PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
     if (!c->deterministic) {
@@ -307,6 +312,9 @@ sft_status sft_update_core(sft_ctx *c, int32_t mode, const int32_t *const *idx, 
     if (st != SFT_OK) return st;
     if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
     if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
+    if (c->cbf16)
+        return fail(c, SFT_ENOTSUP, "the COO core pass needs float32 cached products; use the "
+                                    "slice calls with SFT_BF16");
     if (nnz == 0) return SFT_OK;
     PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
     for (int64_t b0 = 0; b0 < nnz; b0 += batch) {

@@ -2,6 +2,7 @@
 // device helpers shared by the CUDA translation units of the library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,7 @@ struct PassArgs {
     float *B;                       // B^(n), J_n x R
     float lr, lam;
     int *err;                       // device error flag
+    int cbf16;                      // cached products C^(k) are stored as bfloat16
     // the N-1 modes other than n, in ascending order (set when n >= 0)
     const int32_t *oidx[kMaxOrder];
     const float *oC[kMaxOrder];
@@ -52,7 +54,7 @@ constexpr int64_t kDetMaxBatch = 16384;  // largest deterministic factor minibat
 // Each returns cudaGetLastError() after enqueuing.  J and R are validated by
 // the caller (sft_api.cu) against the supported set.
 cudaError_t launch_refresh(const float *A, const float *B, float *C, int64_t I, int J, int R,
-                           cudaStream_t st, int sms);
+                           bool cbf16, cudaStream_t st, int sms);
 cudaError_t launch_factor_hogwild(const PassArgs &a, int J, int R, cudaStream_t st, int sms);
 cudaError_t launch_factor_det(const PassArgs &a, int J, int R, const DetFactorWs &ws,
                               cudaStream_t st);
@@ -112,6 +114,44 @@ __device__ __forceinline__ bool sample_at(const PassArgs &a, int64_t pos, int64_
         s = pos;
     }
     return true;
+}
+
+// Four consecutive cached-product entries starting at element `off` of a C
+// array stored as CT (float or bfloat16), widened to float (bf16 -> f32 is
+// exact: the bf16 bits are the top half of the f32).
+template <typename CT>
+__device__ __forceinline__ float4 ldC(const float *base, int64_t off);
+
+template <>
+__device__ __forceinline__ float4 ldC<float>(const float *base, int64_t off) {
+    return ldg4(base + off);
+}
+
+template <>
+__device__ __forceinline__ float4 ldC<__nv_bfloat16>(const float *base, int64_t off) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(
+        reinterpret_cast<const __nv_bfloat16 *>(base) + off));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+// Stores four floats as CT at element `off` (bf16: round to nearest even).
+template <typename CT>
+__device__ __forceinline__ void stC(float *base, int64_t off, float4 v);
+
+template <>
+__device__ __forceinline__ void stC<float>(float *base, int64_t off, float4 v) {
+    *reinterpret_cast<float4 *>(base + off) = v;
+}
+
+template <>
+__device__ __forceinline__ void stC<__nv_bfloat16>(float *base, int64_t off, float4 v) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&lo);
+    u.y = *reinterpret_cast<const uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(base) + off) = u;
 }
 
 // Load a run of L consecutive floats (L in {1,2,4,8,...}) from a 4L-byte

@@ -45,7 +45,7 @@ struct Rows {
 
 // Checks the coordinates of a sample (they have arrived by now), reports bad
 // data, and gathers the lane's float4 of every other mode's cached row.
-template <int NO, int R, bool WITH_ROW = false>
+template <int NO, int R, typename CT, bool WITH_ROW = false>
 __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c, int sub,
                                           Rows<NO> &w, bool &ok, int32_t &row) {
     bool bad = false;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c
     ok = c.valid && !bad;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (ok && q < a.N - 1) ? ldg4(a.oC[q] + (int64_t)c.i[q] * R + 4 * sub)
+        w.r[q] = (ok && q < a.N - 1) ? ldC<CT>(a.oC[q], (int64_t)c.i[q] * R + 4 * sub)
                                      : make_float4(1.f, 1.f, 1.f, 1.f);
 }
 
@@ -84,7 +84,7 @@ struct WalkDepth {
 // Calls body(x, ok, p) for slice-ordered positions [s0, s1) in order, where p
 // is the lane's 4 entries of prod_{k != n} C^(k)[i_k][:] and ok says whether
 // the position's data was valid.
-template <int NO, int R, int DMAX, bool WITH_ROW, typename Body>
+template <int NO, int R, typename CT, int DMAX, bool WITH_ROW, typename Body>
 __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, int sub,
                                      Body &&body) {
     // Two-level ring: the cached rows of positions t .. t+D-1 and the raw
@@ -105,7 +105,7 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
             load_sample<NO, WITH_ROW>(a, s0 + D + u, s0 + D + u < s1, cring[u]);
 #pragma unroll
         for (int u = 0; u < D; ++u) {
-            load_rows<NO, R, WITH_ROW>(a, tmp[u], sub, ring[u], rok[u], rrow[u]);
+            load_rows<NO, R, CT, WITH_ROW>(a, tmp[u], sub, ring[u], rok[u], rrow[u]);
             rx[u] = tmp[u].x;
         }
     }
@@ -115,7 +115,7 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
             if (t + u < s1) {
                 body(rrow[u], rx[u], rok[u], product<NO>(ring[u]));
                 // position t + u + D: its coordinates arrived D steps ago
-                load_rows<NO, R, WITH_ROW>(a, cring[u], sub, ring[u], rok[u], rrow[u]);
+                load_rows<NO, R, CT, WITH_ROW>(a, cring[u], sub, ring[u], rok[u], rrow[u]);
                 rx[u] = cring[u].x;
                 load_sample<NO, WITH_ROW>(a, t + u + 2 * D, t + u + 2 * D < s1, cring[u]);
             }
@@ -141,7 +141,7 @@ __device__ __forceinline__ bool slice_ok(const SliceArgs &g, int64_t s, int64_t 
 // Runs positions [s0, s1) of slice r element by element.  The lane holds the
 // JL entries [sub*JL, (sub+1)*JL) of a_r.  The next position's coordinates and
 // cached rows are loaded while the current one is computed.
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, int32_t r,
                                            int64_t s0, int64_t s1, int sub, unsigned m) {
     constexpr int T = R / 4;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
     float av[JL];
     float *arow = a.A + (int64_t)r * J + sub * JL;
     load_run<JL>(arow, av);
-    walk<NB, R, 4, false>(a, s0, s1, sub, [&](int32_t, float x, bool ok, const float4 &p) {
+    walk<NB, R, CT, 4, false>(a, s0, s1, sub, [&](int32_t, float x, bool ok, const float4 &p) {
         float vp[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -216,7 +216,7 @@ constexpr int kSliceThreads = 256;
 // tile's first run if its slice started before the tile and its last run if
 // its slice continues after it; the factor row is switched in place whenever
 // the slice changes.
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles(SliceArgs g) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
         float av[JL];
 #pragma unroll
         for (int q = 0; q < JL; ++q) av[q] = 0.f;
-        walk<NB, R, 4, true>(a, q0, q1, sub, [&](int32_t row, float x, bool ok, const float4 &p) {
+        walk<NB, R, CT, 4, true>(a, q0, q1, sub, [&](int32_t row, float x, bool ok, const float4 &p) {
             if (row != cur) {  // the slice changes: write the finished row, read the next
                 if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
                 cur = row;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
 
 // Crossing slices of at most Lseq nonzeros, whole, one per lane group (the
 // group that owns the slice's first tile boundary).
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chains(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
         int32_t r;
         int64_t s, e;
         if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
-            run_direct<NB, R, J>(g, sB, r, s, e, sub, m);
+            run_direct<NB, R, J, CT>(g, sB, r, s, e, sub, m);
     }
 }
 
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
 // Composes the steps of positions [s0, s1) of one slice into the affine map
 // (M, c) with a_after = M a_before + c.  The lane holds rows [sub*JL, ...) of M
 // and c.
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, int64_t s0,
                                             int64_t s1, int sub, unsigned m, float *out) {
     constexpr int T = R / 4;
@@ -342,7 +342,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         pw = ainv;
         since = 0;
     };
-    walk<NB, R, 2, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
+    walk<NB, R, CT, 2, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
         float v[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -391,7 +391,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 // One group per tile: maps for the tile's first run (if its slice started
 // before the tile) and last run (if its slice continues after the tile) when
 // that slice is longer than Lseq.
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
@@ -420,10 +420,10 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
             // slot 0: run that started before the tile; slot 1: run that starts in
             // the tile and continues after it
             if (side == 0 && before) {
-                compose_map<NB, R, J>(g, sB, p0, min(e, p1), sub, m,
+                compose_map<NB, R, J, CT>(g, sB, p0, min(e, p1), sub, m,
                                       g.maps + (t * 2 + 0) * (int64_t)(J * J + J));
             } else if (side == 1 && after && !before) {
-                compose_map<NB, R, J>(g, sB, max(s, p0), p1, sub, m,
+                compose_map<NB, R, J, CT>(g, sB, max(s, p0), p1, sub, m,
                                       g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
             }
         }
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
 // Dynamic shared memory: B (J*R) then one G tile (J*R) per lane group.
 constexpr int kCoreSliceThreads = 128;
 
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_core(SliceArgs g,
                                                                    float *__restrict__ partials) {
     constexpr int T = R / 4;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
                 *gp = v;
             }
         };
-        walk<NB, R, 4, true>(a, p0, p1, sub, [&](int32_t row, float x0, bool ok0, const float4 &p) {
+        walk<NB, R, CT, 4, true>(a, p0, p1, sub, [&](int32_t row, float x0, bool ok0, const float4 &p) {
             if (row != cur) {  // a new run: close the last one, read a and w = B^T a
                 if (cur >= 0) flush();
                 cur = row;
@@ -528,50 +528,56 @@ inline int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block,
 // The three kernels touch disjoint data (chains and tiles write different
 // factor rows, maps write only the map workspace), so they may run on three
 // streams at once.
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
     if (g.ntiles > 1) {
-        const int gch = grid_for(k_slices_chains<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles - 1, sms);
-        k_slices_chains<NB, R, J><<<gch, kSliceThreads, 0, ss.chains>>>(g);
+        const int gch = grid_for(k_slices_chains<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles - 1, sms);
+        k_slices_chains<NB, R, J, CT><<<gch, kSliceThreads, 0, ss.chains>>>(g);
         *launches += 1;
     }
-    const int gd = grid_for(k_slices_tiles<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
-    k_slices_tiles<NB, R, J><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
+    const int gd = grid_for(k_slices_tiles<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
+    k_slices_tiles<NB, R, J, CT><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
     *launches += 1;
     if (with_maps && g.ntiles > 1) {
-        const int gm = grid_for(k_slices_maps<NB, R, J>, kSliceThreads, 0, gpb, g.ntiles, sms);
-        k_slices_maps<NB, R, J><<<gm, kSliceThreads, 0, ss.maps>>>(g);
+        const int gm = grid_for(k_slices_maps<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
+        k_slices_maps<NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
         *launches += 1;
     }
 }
 
-template <int NB, int R, int J>
+template <int NB, int R, int J, typename CT>
 int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStream_t st,
                          int sms) {
     constexpr int T = R / 4;
     const size_t smem = (size_t)(1 + kCoreSliceThreads / T) * J * R * sizeof(float);
-    cudaFuncSetAttribute(k_slices_core<NB, R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_slices_core<NB, R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    int nblk = grid_for(k_slices_core<NB, R, J>, kCoreSliceThreads, smem, kCoreSliceThreads / T,
+    int nblk = grid_for(k_slices_core<NB, R, J, CT>, kCoreSliceThreads, smem, kCoreSliceThreads / T,
                         g.ntiles, sms);
     if (nblk > max_blocks) nblk = max_blocks;
-    k_slices_core<NB, R, J><<<nblk, kCoreSliceThreads, smem, st>>>(g, partials);
+    k_slices_core<NB, R, J, CT><<<nblk, kCoreSliceThreads, smem, st>>>(g, partials);
     return nblk;
 }
 
 
 // Per-order wrappers (defined in k_slices_f<NO>.cu / k_slices_c<NO>.cu).
-#define SFT_SLICE_WRAPPERS(NO)                                                              \
-    void factor_slices_no##NO(const SliceArgs &g, int R, int J, bool with_maps,            \
-                              const SliceStreams &ss, int sms, int64_t *launches);          \
-    int core_slices_no##NO(const SliceArgs &g, int R, int J, float *partials, int max_blocks, \
-                           cudaStream_t st, int sms);
-SFT_SLICE_WRAPPERS(2)
-SFT_SLICE_WRAPPERS(3)
-SFT_SLICE_WRAPPERS(7)
-SFT_SLICE_WRAPPERS(15)
+// Per-(order bound, C type) wrappers, one translation unit each
+// (k_slices_f<NO>_<ct>.cu, k_slices_c<NO>_<ct>.cu) so they compile in parallel.
+#define SFT_SLICE_WRAPPERS(NO, CTN)                                                         \
+    void factor_slices_no##NO##_##CTN(const SliceArgs &g, int R, int J, bool with_maps,    \
+                                      const SliceStreams &ss, int sms, int64_t *launches);  \
+    int core_slices_no##NO##_##CTN(const SliceArgs &g, int R, int J, float *partials,      \
+                                   int max_blocks, cudaStream_t st, int sms);
+SFT_SLICE_WRAPPERS(2, f32)
+SFT_SLICE_WRAPPERS(3, f32)
+SFT_SLICE_WRAPPERS(7, f32)
+SFT_SLICE_WRAPPERS(15, f32)
+SFT_SLICE_WRAPPERS(2, bf16)
+SFT_SLICE_WRAPPERS(3, bf16)
+SFT_SLICE_WRAPPERS(7, bf16)
+SFT_SLICE_WRAPPERS(15, bf16)
 #undef SFT_SLICE_WRAPPERS
 
 }  // namespace sft

@@ -323,21 +323,24 @@ class Slices:
 class Decomposition:
     """Device-resident FastTucker parameters plus a libsft context.
 
-    A[n] (I_n x J_n), B[n] (J_n x R) and C[n] = A[n] B[n] (I_n x R) are float32
-    torch tensors on the current CUDA device; ``workspace`` is a byte tensor
-    sized by sft_workspace_bytes.  All methods forward to the C ABI."""
+    A[n] (I_n x J_n) and B[n] (J_n x R) are float32 torch tensors on the current
+    CUDA device; C[n] = A[n] B[n] (I_n x R) is float32, or bfloat16 with
+    prec = SFT_BF16; ``workspace`` is a byte tensor sized by
+    sft_workspace_bytes.  All methods forward to the C ABI."""
 
     def __init__(self, A0: Sequence[torch.Tensor], B0: Sequence[torch.Tensor],
                  deterministic: bool = True, max_batch: int = 4096, device="cuda",
-                 stream=None):
+                 stream=None, prec: int = SFT_FP32):
         self.A = [a.to(device=device, dtype=torch.float32).contiguous().clone() for a in A0]
         self.B = [b.to(device=device, dtype=torch.float32).contiguous().clone() for b in B0]
         self.N = len(self.A)
         self.R = int(self.B[0].shape[1])
         self.dims = [int(a.shape[0]) for a in self.A]
         self.J = [int(a.shape[1]) for a in self.A]
-        self.C = [torch.empty(i, self.R, device=device, dtype=torch.float32) for i in self.dims]
-        self.cfg = make_config(self.dims, self.J, self.R, deterministic, SFT_FP32, stream)
+        self.prec = prec
+        cdt = torch.bfloat16 if prec == SFT_BF16 else torch.float32
+        self.C = [torch.empty(i, self.R, device=device, dtype=cdt) for i in self.dims]
+        self.cfg = make_config(self.dims, self.J, self.R, deterministic, prec, stream)
         nbytes = sft_workspace_bytes(self.cfg, max_batch)
         if nbytes == 0:
             raise SftError(SFT_EINVAL, "sft_workspace_bytes rejected the configuration")

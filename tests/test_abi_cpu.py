@@ -56,7 +56,8 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     ((10, 10), (8, 8), 12, 0, "ENOTSUP"),     # R not supported
     ((10, 10), (8, 6), 8, 0, "ENOTSUP"),      # J not supported
     ((10, 10), (4, 4), 32, 0, "ENOTSUP"),     # 4J < R
-    ((10, 10), (8, 8), 8, 1, "ENOTSUP"),      # bf16 not in this build
+    ((10, 10), (8, 8), 8, 1, "ok"),           # bfloat16 cached products
+    ((10, 10), (8, 8), 8, 7, "EINVAL"),       # unknown precision
     ((0, 10), (8, 8), 8, 0, "EINVAL"),        # empty mode
 ])
 def test_config_validation(lib, dims, J, R, prec, want):

@@ -223,3 +223,82 @@ def test_slices_bitwise_reproducible(sft, skewed):
         outs.append([t.clone() for t in dec.A + dec.B])
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+# ----------------------------------------------------------------------------- bfloat16 cached products
+
+TOL_BF16 = 2e-2
+
+
+def test_bf16_refresh_and_predictions(sft, oracle_mod):
+    """C stored in bfloat16: C and predictions within 2e-2 of the float64 oracle
+    (condition-aware); the measured worst ratio is printed as the result's error."""
+    T = small_tensor()
+    idx, val = to_dev(T)
+    dec = sft.Decomposition(T.A0, T.B0, prec=sft.SFT_BF16)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    from parity_util import abs_C, pred_scale
+    absC = abs_C(ref.A, ref.B)
+    worst = 0.0
+    for n in range(3):
+        got = dec.C[n].float().cpu().numpy()
+        assert_within(got, ref.C[n], absC[n], tol=TOL_BF16, what=f"bf16 C^({n})")
+        worst = max(worst, float(np.max(np.abs(got - ref.C[n]) / (absC[n] + 1e-30))))
+    ix = np_idx(T.idx)
+    xh = dec.predict(idx).cpu().numpy()
+    scale = pred_scale(absC, ix)
+    assert_within(xh, ref.predict(ix), scale, tol=TOL_BF16, what="bf16 x^")
+    print(f"bf16: worst |C err|/|A||B| = {worst:.3e}, "
+          f"worst |x^ err|/scale = {float(np.max(np.abs(xh - ref.predict(ix)) / scale)):.3e}")
+
+
+def test_bf16_slice_passes(sft, oracle_mod):
+    """One factor pass (element by element) and one whole-pass core step per mode
+    with bfloat16 cached products track the float64 oracle within 2e-2."""
+    T = small_tensor()
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0, prec=sft.SFT_BF16)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        A0 = dec.A[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, None)
+        dec.update_factors_slices(sl, lr=0.05, lam=0.01)
+        dec.refresh(n)
+        ref.factor_pass(n, ix, T.val.numpy(), batch=1, lr=0.05, lam=0.01)
+        ref.refresh(n)
+        dec.sync(60_000)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert rel_fro(got - A0, ref.A[n] - A0) < TOL_BF16, n
+    for n in range(3):
+        B0 = dec.B[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, None)
+        dec.update_core_slices(sl, batch=T.nnz, lr=1.0, lam=0.01)
+        dec.refresh(n)
+        ref.core_pass(n, ix, T.val.numpy(), batch=T.nnz, lr=1.0, lam=0.01)
+        ref.refresh(n)
+        dec.sync(60_000)
+        got = dec.B[n].cpu().numpy().astype(np.float64)
+        assert rel_fro(got - B0, ref.B[n] - B0) < TOL_BF16, n
+
+
+def test_bf16_epochs_rmse(sft, oracle_mod, skewed):
+    """Two epochs on the Zipf tensor with bfloat16 cached products: training RMSE
+    within 1 % of the float64 oracle per epoch."""
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    xv = T.val.numpy()
+    dec = sft.Decomposition(T.A0, T.B0, prec=sft.SFT_BF16)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    lays = [dec.slices(n, idx, val, None) for n in range(3)]
+    for ep in range(2):
+        for n in range(3):
+            dec.update_factors_slices(lays[n], lr=0.01, lam=0.01)
+            dec.refresh(n)
+        for n in range(3):
+            dec.update_core_slices(lays[n], lr=0.01, lam=0.01)
+            dec.refresh(n)
+        ref.epoch(ix, xv, None, None, batch_factor=1, batch_core=T.nnz)
+        got, want = dec.rmse(idx, val), ref.rmse(ix, xv)
+        assert abs(got / want - 1) < 0.01, (ep, got, want)
