@@ -70,6 +70,9 @@ def _load():
             lib.orc_core_pass.restype = ctypes.c_int
             lib.orc_loss.argtypes = [ctypes.c_int, ctypes.c_int, _pp_d, _pp_i32, fp, i64, _dp, _dp]
             lib.orc_loss.restype = None
+            lib.orc_loss_grad.argtypes = [ctypes.c_int, ip64, ip32, ctypes.c_int, _pp_d, _pp_d,
+                                          _pp_d, _pp_i32, fp, i64, _pp_d, _pp_d]
+            lib.orc_loss_grad.restype = ctypes.c_double
             lib.orc_epoch.argtypes = [ctypes.c_int, ip64, ip32, ctypes.c_int, _pp_d, _pp_d, _pp_d,
                                       _pp_i32, fp, i64, _pp_u32, _pp_u32, i64, i64, d, d, d, d]
             lib.orc_epoch.restype = ctypes.c_int
@@ -186,6 +189,21 @@ class Model:
                          val.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(val),
                          ctypes.byref(sse), ctypes.byref(sae))
         return sse.value, sae.value
+
+    def loss_grad(self, idx, val):
+        """(L, gA, gB): L = 1/2 sum e^2 over the nonzeros and its gradient with
+        respect to every A[n] and B[n] (Eq. (10)/(11) without regularisation)."""
+        idx, val = self._coo(idx, val)
+        gA = [np.zeros_like(a) for a in self.A]
+        gB = [np.zeros_like(b) for b in self.B]
+        A, B, C = self._arrays()
+        J = np.ascontiguousarray(self.J, dtype=np.int32)
+        L = _load().orc_loss_grad(self.N, self.I.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  J.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.R, A, B, C,
+                                  _ptr_array(idx, ctypes.c_int32),
+                                  val.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(val),
+                                  _ptr_array(gA, ctypes.c_double), _ptr_array(gB, ctypes.c_double))
+        return L, gA, gB
 
     def rmse(self, idx, val) -> float:
         sse, _ = self.loss(idx, val)

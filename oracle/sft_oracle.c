@@ -276,6 +276,44 @@ void orc_loss(int N, int R, const double *const *C, const int32_t *const *idx,
     *sae = s1;
 }
 
+/* Gradient of the sampled loss L = 1/2 sum_s (x_s - x^_s)^2 (the data term of
+ * Eq. (6) with the factor 2 absorbed, as in Eq. (10)/(11)) with respect to
+ * every factor and core matrix, summed over the nonzeros:
+ *   dL/da^(n)_{i_n} = -sum_{s: i_n(s) = i_n} e_s v^(n)_s,   v^(n)_s = B^(n) p^(n)_s
+ *   dL/dB^(n)       = -sum_s e_s a^(n)_{i_n(s)} p^(n)_s^T
+ * (Eq. (10) and Eq. (11) without the regulariser).  gA[n] (I_n x J_n) and
+ * gB[n] (J_n x R) are overwritten.  Also returns L. */
+double orc_loss_grad(int N, const int64_t *I, const int *J, int R, const double *const *A,
+                     const double *const *B, const double *const *C,
+                     const int32_t *const *idx, const float *val, int64_t nnz,
+                     double *const *gA, double *const *gB)
+{
+    for (int n = 0; n < N; ++n) {
+        memset(gA[n], 0, sizeof(double) * (size_t)I[n] * J[n]);
+        memset(gB[n], 0, sizeof(double) * (size_t)J[n] * R);
+    }
+    double *p = malloc(sizeof(double) * R);
+    double *v = malloc(sizeof(double) * 64);
+    double loss = 0.0;
+    for (int64_t s = 0; s < nnz; ++s) {
+        const double e = (double)val[s] - predict_cached(N, R, C, idx, s);
+        loss += 0.5 * e * e;
+        for (int n = 0; n < N; ++n) {
+            const int64_t i = idx[n][s];
+            hadamard_others(N, R, n, C, idx, s, p);
+            core_times(J[n], R, B[n], p, v);
+            for (int j = 0; j < J[n]; ++j) {
+                gA[n][i * J[n] + j] -= e * v[j];
+                for (int r = 0; r < R; ++r)
+                    gB[n][(int64_t)j * R + r] -= e * A[n][i * J[n] + j] * p[r];
+            }
+        }
+    }
+    free(p);
+    free(v);
+    return loss;
+}
+
 /* One epoch of Algorithm 2: the factor module over every mode (each followed
  * by a refresh of that mode's cached product), then the core module over every
  * mode (each followed by a refresh).  perm_factor[n] / perm_core[n] give the

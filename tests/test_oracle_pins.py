@@ -349,3 +349,40 @@ def test_planted_recovery(oracle_mod):
         if hist[-1] < 0.05 * std:
             break
     assert hist[-1] < 0.05 * std, (std, hist[::20])
+
+
+# ----------------------------------------------------------------------------- loss gradient
+
+
+def test_loss_gradient_is_central_difference(oracle_mod):
+    """dL/dA and dL/dB of L = 1/2 sum e^2 match central differences of the
+    dense-reconstruction loss (h = 1e-6) for every entry of every matrix."""
+    rng = np.random.default_rng(13)
+    I, J, R = (4, 3, 5), (2, 3, 2), 3
+    A, B = rand_model(rng, I, J, R)
+    idx, val = rand_coo(rng, I, 20)
+    m = oracle_mod.Model(A, B)
+    L, gA, gB = m.loss_grad(idx, val)
+
+    def f(As, Bs):
+        X = dense_tucker(As, Bs)
+        e = val.astype(np.float64) - X[tuple(idx)]
+        return 0.5 * np.sum(e * e)
+
+    assert abs(L - f(A, B)) <= 1e-12 * abs(L)
+    h = 1e-6
+    for n in range(3):
+        for i in range(I[n]):
+            for j in range(J[n]):
+                Ap, Am = [a.copy() for a in A], [a.copy() for a in A]
+                Ap[n][i, j] += h
+                Am[n][i, j] -= h
+                fd = (f(Ap, B) - f(Am, B)) / (2 * h)
+                assert abs(gA[n][i, j] - fd) <= 1e-7 * (1 + abs(fd))
+        for j in range(J[n]):
+            for r in range(R):
+                Bp, Bm = [b.copy() for b in B], [b.copy() for b in B]
+                Bp[n][j, r] += h
+                Bm[n][j, r] -= h
+                fd = (f(A, Bp) - f(A, Bm)) / (2 * h)
+                assert abs(gB[n][j, r] - fd) <= 1e-7 * (1 + abs(fd))
