@@ -54,9 +54,15 @@ def parse():
     p.add_argument("--path", default="slices", choices=["slices", "coo"])
     p.add_argument("--prec", default="fp32", choices=["fp32", "bf16"],
                    help="storage of the cached products C (arithmetic is float32 either way)")
-    p.add_argument("--workload", default="ratings", choices=["ratings", "order8"],
+    p.add_argument("--workload", default="ratings",
+                   choices=["ratings", "order8", "autograd", "batch"],
                    help="ratings: 480000x17800x2200, 100M nnz, J=R=16; order8: 8 modes of "
-                        "10000, 50M nnz, J=R=32")
+                        "10000, 50M nnz, J=R=32; autograd: loss forward + backward over 4 "
+                        "modes of 100000, 20M nnz, J=R=32; batch: 64 independent problems "
+                        "(order 3-6, dims 1k-200k, nnz 10k-5M, J=R in 4..32) in one "
+                        "persistent launch per epoch")
+    p.add_argument("--lr", type=float, default=0.0,
+                   help="SGD step for A and B (0 = 0.01 for ratings, 1e-5 for order8)")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
     p.add_argument("--slice-max-direct", type=int, default=0,
                    help="longest crossing slice run element by element (0 = automatic)")
@@ -201,6 +207,22 @@ def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0, c_bytes=4):
 # ----------------------------------------------------------------------------- CPU oracle
 
 
+def cpu_oracle_grad_rate(T, sample: int):
+    """Oracle loss and gradient (FP64, single thread) over the first `sample`
+    nonzeros; returns (nonzeros per second, seconds, sample)."""
+    import oracle
+    oracle.build()
+    S = min(sample, T.nnz)
+    idx = [i[:S].cpu().numpy() for i in T.idx]
+    val = T.val[:S].cpu().numpy()
+    m = oracle.Model([a.cpu().numpy() for a in T.A0], [b.cpu().numpy() for b in T.B0])
+    t0 = time.perf_counter()
+    m.refresh_all()
+    m.loss_grad(idx, val)
+    dt = time.perf_counter() - t0
+    return S / dt, dt, S
+
+
 def cpu_oracle_epoch_rate(T, sample: int):
     """Oracle (FP64, single thread) on the first `sample` training nonzeros with
     the same schedule (factor rows element by element, core once per pass);
@@ -218,6 +240,281 @@ def cpu_oracle_epoch_rate(T, sample: int):
     return S / dt, dt, S
 
 
+# ----------------------------------------------------------------------------- batch
+
+
+def stable_lrs(Ts, cap, c=0.5):
+    """Per-problem SGD step kept below c / max_s |v_s|^2 at the initial
+    parameters (one step scales a row along v by 1 - lr |v|^2; the products of
+    N - 1 cached rows are heavy-tailed at high order and rank).  Setup only."""
+    out = []
+    for T in Ts:
+        A = [a.double() for a in T.A0]
+        B = [b.double() for b in T.B0]
+        C = [a @ b for a, b in zip(A, B)]
+        vmax = 0.0
+        for n in range(len(A)):
+            p = None
+            for k in range(len(A)):
+                if k != n:
+                    rows = C[k][T.idx[k].long()]
+                    p = rows if p is None else p * rows
+            v = p @ B[n].T
+            vmax = max(vmax, float((v * v).sum(1).max()))
+            del p, v
+        out.append(min(cap, c / vmax) if vmax > 0 else cap)
+    return out
+
+
+def run_batch(args, world, rank, lr):
+    """One step = one epoch of Algorithm 2 for each of 64 independent problems
+    (one graph launch of the persistent kernel; tiles autotuned first)."""
+    from paper_2210_06014_gb300 import synth
+    specs = synth.spec_batch(64, seed=0)
+    total_nnz = sum(s.nnz for s in specs)
+    metric = "SGD nonzeros/s (factor+core updates)"
+    unit = "nnz/s"
+    workload = f"batch64-order3to6-dims1k-200k-nnz10k-5M-R4to32 ({total_nnz} nnz)"
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        big = max(specs, key=lambda s: s.nnz)
+        T = synth.make_tensor(big, device="cuda" if torch.cuda.is_available() else "cpu")
+        steps = []
+        for i in range(args.warmup + args.steps):
+            rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4))
+            if i >= args.warmup:
+                steps.append((rate, dt))
+        rate = statistics.median(r for r, _ in steps)
+        print(json.dumps({
+            "impl": "reference", "metric": metric, "value": rate, "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(d for _, d in steps) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload, "sample_nnz": S},
+            "cpu_baseline": {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": f"first {S} nonzeros of the largest problem, one epoch"},
+            "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    from paper_2210_06014_gb300 import sft
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    Ts = [synth.make_tensor(s, device=dev) for s in specs]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    prec = sft.SFT_BF16 if args.prec == "bf16" else sft.SFT_FP32
+    lrs = stable_lrs(Ts, lr)
+    b = sft.Batch([(T.A0, T.B0, list(T.idx), T.val) for T in Ts], prec=prec, min_chunk=1024,
+                  lr=lrs, lam=0.01)
+    t0 = time.perf_counter()
+    chunk, bps = b.autotune(epochs=2)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.epoch()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = b.launches
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            b.epoch()
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = (b.launches - l0) * 2  # counter reset + persistent kernel per graph
+    b.sync(600_000)
+    elapsed = start.elapsed_time(end) / 1e3
+    elapsed_max = max_over_ranks(elapsed, world)
+    value = replica_rate(total_nnz * args.steps, elapsed, world)
+    c_bytes = 2 if args.prec == "bf16" else 4
+    byts = 0.0
+    for s in specs:
+        fac, core = algorithmic_bytes(s.order, s.R, s.R, "coo", 1.0, c_bytes)
+        byts += s.order * s.nnz * (fac + core)
+        byts += 2 * sum(I * (s.R + s.R) * 4 for I in s.dims)  # two refreshes per mode
+    ep_s = elapsed / args.steps
+    peak, peak_kind = peaks()
+    ach = byts / ep_s / 1e9
+    rmse = b.rmse()
+
+    e2e = None
+    if not args.no_e2e:
+        dev_in = [t for T in Ts for t in list(T.idx) + [T.val]]
+        host_in = [t.cpu().pin_memory() for t in dev_in]
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            for d, h in zip(dev_in, host_in):
+                d.copy_(h, non_blocking=True)
+            b.epoch()
+            b.loss()  # synchronises and reads the per-problem sums back
+        et = max_over_ranks(time.perf_counter() - t1, world)
+        e2e = {"value": sum_over_ranks(float(total_nnz * args.steps), world) / et, "unit": unit,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * len(specs),
+               "includes": "input copies, epoch, loss pass and its readback"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        big = max(range(len(specs)), key=lambda i: specs[i].nnz)
+        rate, dt, S = cpu_oracle_epoch_rate(Ts[big], args.cpu_sample)
+        cpu = {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"first {S} nonzeros of the largest problem, one epoch ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "c_storage": args.prec,
+            "config": {
+                "workload": workload, "problems": len(specs), "nnz": total_nnz,
+                "parallelism": "replicas only" if world > 1 else "single GPU",
+                "schedule": "per problem: Hogwild factor pass + refresh per mode, then whole-pass "
+                            "core update + refresh per mode; all problems in one persistent "
+                            "launch (CUDA graph)",
+                "autotuned": {"chunk": chunk, "blocks_per_sm": bps, "seconds": round(tune_s, 2)},
+                "epoch_tasks": b.epoch_tasks,
+                "lr": {"rule": "min(cap, 0.5 / max |v|^2 at init) per problem", "cap": lr,
+                       "min": min(lrs), "max": max(lrs)},
+                "lambda": 0.01,
+                "l2": "inputs larger than L2", "generation_s": round(gen_s, 2),
+                "train_rmse_after": {"min": min(rmse), "median": statistics.median(rmse),
+                                     "max": max(rmse)},
+            },
+            "roofline": {"bound": "hbm", "kernel": "persistent batch kernel", "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "peak_source": peak_kind},
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- autograd
+
+
+def run_autograd(args, world, rank, sft, T, spec, metric, unit, gen_s):
+    """One step = forward + backward of the sampled loss L = 1/2 sum e^2 over
+    every nonzero through sft.SampledLoss (refresh of every C^(n), the fused
+    loss + dL/dC pass, then dL/dA and dL/dB for every mode)."""
+    dev = T.val.device
+    N, J, R = spec.order, spec.J[0], spec.R
+    nnz = T.nnz
+    idx, val = list(T.idx), T.val
+    prec = sft.SFT_BF16 if args.prec == "bf16" else sft.SFT_FP32
+    mod = sft.SampledLoss(T.A0, T.B0, prec=prec)
+    stream = torch.cuda.current_stream()
+    fw, bw = [], []
+
+    def step(timed, src=None):
+        if src is not None:
+            for d, h in zip(src[0], src[1]):
+                d.copy_(h, non_blocking=True)
+        for p in mod.parameters():
+            p.grad = None
+        if timed:
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+        loss = mod(idx, val)
+        if timed:
+            b.record(stream)
+        loss.backward()
+        if timed:
+            c.record(stream)
+            fw.append((a, b))
+            bw.append((b, c))
+        return loss
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = mod.dec.launches
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            loss = step(True)
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = mod.dec.launches - launches0
+    mod.dec.sync(600_000)
+    elapsed = start.elapsed_time(end) / 1e3
+    elapsed_max = max_over_ranks(elapsed, world)
+    total_nnz = sum_over_ranks(float(nnz * args.steps), world)
+    value = replica_rate(nnz * args.steps, elapsed, world)
+    f_ms = sum(a.elapsed_time(b) for a, b in fw) / len(fw)
+    b_ms = sum(a.elapsed_time(b) for a, b in bw) / len(bw)
+    # forward: COO entry, N gathered C rows, one R-float gradient row per mode
+    fwd_bytes = 4 * N + 4 + N * R * 4 + N * R * 4
+    peak, peak_kind = peaks()
+    ach = fwd_bytes * nnz / (f_ms / 1e3) / 1e9
+    loss_v = float(loss.item())
+
+    e2e = None
+    if not args.no_e2e:
+        dev_in = idx + [val]
+        host_in = [t.cpu().pin_memory() for t in dev_in]
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        hl = torch.zeros(1, dtype=torch.float64).pin_memory()
+        step(False, (dev_in, host_in))
+        torch.cuda.synchronize()
+        barrier(world)
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(args.steps):
+            loss = step(False, (dev_in, host_in))
+            hl.copy_(loss.detach().reshape(1), non_blocking=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        et = max_over_ranks(s2.elapsed_time(e2) / 1e3, world)
+        e2e = {"value": total_nnz / et, "unit": unit, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, S = cpu_oracle_grad_rate(T, args.cpu_sample)
+        cpu = {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"first {S} nonzeros, refresh + loss + gradient ({dt:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "c_storage": args.prec,
+            "config": {
+                "workload": spec.name, "nnz": nnz, "J": J, "R": R,
+                "parallelism": "replicas only" if world > 1 else "single GPU",
+                "schedule": "SampledLoss forward (refresh C, fused loss + dL/dC) and backward "
+                            "(dL/dA, dL/dB) over every nonzero",
+                "l2": "inputs larger than L2 (COO 400 MB)", "generation_s": round(gen_s, 2),
+                "loss": loss_v,
+                "per_step_ms": {"forward": f_ms, "backward": b_ms},
+                "algorithmic_bytes_per_nnz": {"forward": fwd_bytes},
+            },
+            "roofline": {"bound": "hbm", "kernel": "forward (loss + dL/dC scatter)",
+                         "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_source": peak_kind},
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- main
 
 
@@ -226,14 +523,29 @@ def main():
     world, rank, local = dist_setup(args)
     from paper_2210_06014_gb300 import synth
 
+    lr = args.lr
     if args.workload == "order8":
         spec = synth.spec_order(8, 10_000, args.nnz if args.nnz != 100_000_000 else 50_000_000, 32)
         spec.test_fraction = 0.1
+        # the products of 7 cached rows are heavy-tailed (max |v|^2 ~ 3e4 per 2M
+        # nonzeros at this init); per-element SGD needs lr |v|^2 < 2
+        lr = lr or 1e-5
+    elif args.workload == "batch":
+        spec = None
+        lr = lr or 0.01
+    elif args.workload == "autograd":
+        spec = synth.spec_order(4, 100_000, args.nnz if args.nnz != 100_000_000 else 20_000_000, 32)
+        spec.test_fraction = 0.0
     else:
         spec = synth.spec_ratings(nnz=args.nnz)
+        lr = lr or 0.01
+    if args.workload == "batch":
+        return run_batch(args, world, rank, lr)
     workload = spec.name
     N, J, R = spec.order, spec.J[0], spec.R
     metric = "SGD nonzeros/s (factor+core updates)"
+    if args.workload == "autograd":
+        metric = "loss forward+backward nonzeros/s"
     unit = "nnz/s"
 
     if args.impl == "reference":
@@ -244,7 +556,10 @@ def main():
         gen_s = time.perf_counter() - t0
         steps = []
         for i in range(args.warmup + args.steps):
-            rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4))
+            if args.workload == "autograd":
+                rate, dt, S = cpu_oracle_grad_rate(T, max(10_000, args.cpu_sample // 4))
+            else:
+                rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4))
             if i >= args.warmup:
                 steps.append((rate, dt))
         rate = statistics.median(r for r, _ in steps)
@@ -255,7 +570,9 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": workload, "sample_nnz": S, "generation_s": gen_s},
                 "cpu_baseline": {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
-                                 "sample": f"first {S} training nonzeros, one epoch"},
+                                 "sample": f"first {S} training nonzeros, " + (
+                                     "loss and gradient" if args.workload == "autograd"
+                                     else "one epoch")},
                 "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -268,6 +585,8 @@ def main():
     T = synth.make_tensor(spec, device=dev)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+    if args.workload == "autograd":
+        return run_autograd(args, world, rank, sft, T, spec, metric, unit, gen_s)
     idx, val = T.idx, T.val
     tidx, tval = T.test_idx, T.test_val
     nnz, ntest = T.nnz, int(tval.numel())
@@ -310,9 +629,9 @@ def main():
                 a, b = ev_pair("factor")
                 a.record(stream)
             if slices:
-                dec.update_factors_slices(slices[n], lr=0.01, lam=0.01)
+                dec.update_factors_slices(slices[n], lr=lr, lam=0.01)
             else:
-                dec.update_factors(n, idx, val, None, batch=4096, lr=0.01, lam=0.01)
+                dec.update_factors(n, idx, val, None, batch=4096, lr=lr, lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
@@ -325,9 +644,9 @@ def main():
                 a, b = ev_pair("core")
                 a.record(stream)
             if slices:
-                dec.update_core_slices(slices[n], batch=core_batch, lr=0.01, lam=0.01)
+                dec.update_core_slices(slices[n], batch=core_batch, lr=lr, lam=0.01)
             else:
-                dec.update_core(n, idx, val, None, batch=core_batch, lr=0.01, lam=0.01)
+                dec.update_core(n, idx, val, None, batch=core_batch, lr=lr, lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
@@ -424,6 +743,7 @@ def main():
             "c_storage": args.prec,
             "config": {
                 "workload": workload, "train_nnz": nnz, "test_nnz": ntest, "J": J, "R": R,
+                "lr": lr, "lambda": 0.01,
                 "parallelism": "replicas only" if world > 1 else "single GPU",
                 "path": args.path,
                 "schedule": ("factor: every mode-n slice element by element (Algorithm 4 order, "

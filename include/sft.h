@@ -153,6 +153,38 @@ sft_status sft_epoch(sft_ctx *ctx, const int32_t *const *idx, const float *val, 
                      float lr_B, float lambda_B);
 
 /* ---------------------------------------------------------------------------
+ * Gradient of the sampled loss.  L = 1/2 sum_s e_s^2 over a COO set is the
+ * data term of the objective in Section "Sparse FastTucker Decomposition"
+ * (the factor 2 absorbed, as in Eq. (10)/(11)).  Its gradient with respect to
+ * A^(n) and B^(n) is Eq. (10) and Eq. (11) without the regulariser, summed
+ * over the set.  Because x^ depends on A^(n), B^(n) only through
+ * C^(n) = A^(n) B^(n) (Eq. (12)), it is computed in two calls:
+ *   dL/dC^(n) = -sum_s e_s [rows i_n(s)] p^(n)_s  (one pass, all modes),
+ *   dL/dA^(n) = dL/dC^(n) B^(n)T,  dL/dB^(n) = A^(n)T dL/dC^(n).
+ * Both read C^(k) as it stands; call sft_refresh_C(ctx, -1) first if A or B
+ * changed.
+ * ------------------------------------------------------------------------- */
+
+/* loss_out (DEVICE, 8-byte aligned, 2 doubles) receives {L, sum_s |e_s|}.
+ * dC: host array of N device pointers; dC[n] is I_n x R float32 row-major,
+ * 16-byte aligned, owned by the caller; dC = NULL computes loss_out only.  accumulate = 0 overwrites dC (zeroed
+ * first); accumulate != 0 adds to what is there.  The per-row sums use float
+ * atomic adds, so dC is not bitwise reproducible from run to run (with either
+ * value of the config's deterministic flag); loss_out is.  Coordinates out
+ * of range are skipped and raise the error flag that sft_sync reports.
+ * Enqueues only. */
+sft_status sft_loss_grad_C(sft_ctx *ctx, const int32_t *const *idx, const float *val, int64_t nnz,
+                           float *const *dC, int32_t accumulate, double *loss_out);
+
+/* gA[n] = s dC[n] B^(n)T (I_n x J_n) and gB[n] = s A^(n)T dC[n] (J_n x R) for
+ * every mode, float32, overwritten; s = *scale, a DEVICE double (the incoming
+ * gradient of L), or 1 when scale is NULL.  dC[n] as produced by
+ * sft_loss_grad_C.  gB is summed over row blocks in a fixed order.
+ * Enqueues only. */
+sft_status sft_grad_AB(sft_ctx *ctx, const float *const *dC, const double *scale, float *const *gA,
+                       float *const *gB);
+
+/* ---------------------------------------------------------------------------
  * Slice layout.  A "slice" of mode n is the set of nonzeros that share the
  * coordinate i_n -- the first level of the CSF tree of Section "Tensor
  * Storage Format".  The sliced copy of a COO set holds the same nonzeros

@@ -1,0 +1,72 @@
+// batch_internal.cuh -- device-side records of the batched runner (many
+// independent decompositions driven by one persistent kernel): the problem
+// table, the task list and the kernel arguments.  Shared by k_batch.cu (the
+// kernel) and sft_batch.cu (plan building, graph capture, autotuning).
+#pragma once
+
+#include <stdint.h>
+
+#include "sft_internal.cuh"
+
+namespace sft {
+
+constexpr int kBatchMaxOrder = 8;
+constexpr int kBatchThreads = 256;
+
+// One decomposition.  J_n = R for every mode.  Pointers are device pointers
+// borrowed from the caller; C[k] holds float or bfloat16 entries.
+struct BatchProblem {
+    const int32_t *idx[kBatchMaxOrder];
+    float *A[kBatchMaxOrder];
+    float *B[kBatchMaxOrder];
+    float *C[kBatchMaxOrder];
+    int32_t dims[kBatchMaxOrder];
+    const float *val;
+    float *partials;   // core-gradient partials, one R x R slot per core task
+    double *lpart;     // loss partials, two doubles per loss task
+    double *loss_out;  // {sum e^2, sum |e|}
+    int64_t nnz;
+    int32_t N, R;
+    float lrA, lamA, lrB, lamB;
+};
+
+enum BatchKind : int32_t {
+    kTaskFactor = 0,   // Hogwild SGD over a chunk of nonzeros (Algorithm 4; Eq. (10))
+    kTaskRefresh = 1,  // rows [begin, end) of C^(n) = A^(n) B^(n) (Algorithm 3)
+    kTaskCore = 2,     // core-gradient partial of a chunk (Eq. (11)) into slot `slot`
+    kTaskApply = 3,    // B^(n) += lr (sum of `nslots` partials / nnz - lambda B^(n)) (Algorithm 5)
+    kTaskLoss = 4,     // residual sums of a chunk into loss slot `slot`
+    kTaskLossFin = 5,  // sum of `nslots` loss slots into loss_out
+};
+
+struct BatchTask {
+    int32_t prob;
+    int32_t kind;
+    int32_t mode;
+    int32_t wait;     // counter that must reach 0 before the task starts (-1: none)
+    int32_t done;     // counter decremented when the task has finished
+    int32_t slot;     // partial slot written by a core / loss task
+    int32_t nslots;   // slots summed by an apply / loss-final task
+    int32_t pad;
+    int64_t begin, end;
+};
+
+struct BatchArgs {
+    const BatchProblem *probs;
+    const BatchTask *tasks;
+    int32_t ntasks;
+    int32_t *counters;      // live counters of this plan
+    const int32_t *init;    // their starting values
+    int32_t ncounters;
+    int32_t *head;          // next task to hand out
+    int32_t *abort;         // set when a wait gave up; every CTA then stops
+    int *err;               // error flag bits (kErrIndex, kErrWait)
+    int64_t wait_limit;     // polls before a wait gives up
+};
+
+constexpr int kErrWait = 4;  // a dependency wait ran out of polls
+
+cudaError_t launch_batch(const BatchArgs &g, bool cbf16, int grid, cudaStream_t st);
+int batch_blocks_per_sm(bool cbf16);
+
+}  // namespace sft

@@ -397,6 +397,48 @@ sft_status sft_predict(sft_ctx *c, const int32_t *const *idx, int64_t nnz, float
     return SFT_OK;
 }
 
+sft_status sft_loss_grad_C(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz,
+                           float *const *dC, int32_t accumulate, double *loss_out) {
+    if (!c) return SFT_EINVAL;
+    sft_status st = check_set(c, idx, val, nnz);
+    if (st != SFT_OK) return st;
+    if (dC)
+        for (int n = 0; n < c->N; ++n)
+            if (!dC[n] || !aligned16(dC[n]))
+                return fail(c, SFT_EINVAL, "dC[n] is NULL or not 16-byte aligned");
+    if (!loss_out || ((uintptr_t)loss_out & 7u)) return fail(c, SFT_EINVAL, "loss_out is NULL or misaligned");
+    PassArgs a = pass_args(c, -1, idx, val, nullptr, nnz, 0.f, 0.f);
+    GradBufs g{};
+    for (int n = 0; n < c->N; ++n) {
+        g.dC[n] = dC ? dC[n] : nullptr;
+        g.dims[n] = c->dims[n];
+    }
+    int nblk = loss_blocks_for(nnz, c->sms);
+    if (nblk > c->loss_max_blocks) nblk = c->loss_max_blocks;
+    cudaError_t e = launch_loss_grad(a, g, c->R, accumulate != 0, c->loss_partials, nblk, loss_out,
+                                     c->stream, c->sms, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "loss gradient launch");
+    return SFT_OK;
+}
+
+sft_status sft_grad_AB(sft_ctx *c, const float *const *dC, const double *scale, float *const *gA,
+                       float *const *gB) {
+    if (!c) return SFT_EINVAL;
+    if (!dC || !gA || !gB) return fail(c, SFT_EINVAL, "dC / gA / gB array is NULL");
+    for (int n = 0; n < c->N; ++n) {
+        if (!dC[n] || !gA[n] || !gB[n]) return fail(c, SFT_EINVAL, "dC[n] / gA[n] / gB[n] is NULL");
+        if (!aligned16(dC[n])) return fail(c, SFT_EINVAL, "dC[n] is not 16-byte aligned");
+    }
+    if (scale && ((uintptr_t)scale & 7u)) return fail(c, SFT_EINVAL, "scale is misaligned");
+    for (int n = 0; n < c->N; ++n) {
+        cudaError_t e = launch_grad_project(c->A[n], c->B[n], dC[n], c->dims[n], c->J[n], c->R,
+                                            scale, gA[n], gB[n], c->core_partials,
+                                            c->core_max_blocks, c->stream, c->sms, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient projection launch");
+    }
+    return SFT_OK;
+}
+
 sft_status sft_epoch(sft_ctx *c, const int32_t *const *idx, const float *val, int64_t nnz,
                      const uint32_t *const *perm_factor, const uint32_t *const *perm_core,
                      int64_t batch_factor, int64_t batch_core, float lr_A, float lambda_A,

@@ -85,6 +85,17 @@ cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, do
                         cudaStream_t st);
 int loss_blocks_for(int64_t count, int sms);
 cudaError_t launch_predict(const PassArgs &a, int R, float *out, cudaStream_t st, int sms);
+// gradient of the sampled loss (k_grad.cu)
+struct GradBufs {
+    float *dC[kMaxOrder];   // dL/dC^(k), I_k x R float32
+    int64_t dims[kMaxOrder];
+};
+cudaError_t launch_loss_grad(const PassArgs &a, const GradBufs &g, int R, bool accumulate,
+                             double *partials, int nblk, double *out, cudaStream_t st, int sms,
+                             int64_t *launches);
+cudaError_t launch_grad_project(const float *A, const float *B, const float *dC, int64_t I, int J,
+                                int R, const double *scale, float *gA, float *gB, float *partials,
+                                int max_blocks, cudaStream_t st, int sms, int64_t *launches);
 
 // ----------------------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

@@ -30,13 +30,26 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy",
             "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_workspace_bytes",
             "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling",
-            "sft_update_factors_noalloc"]
+            "sft_update_factors_noalloc", "sft_loss_grad_C", "sft_grad_AB",
+            "sft_batch_workspace_bytes", "sft_batch_create", "sft_batch_refresh",
+            "sft_batch_epoch", "sft_batch_loss", "sft_batch_snapshot_bytes", "sft_batch_autotune",
+            "sft_batch_sync", "sft_batch_launch_count", "sft_batch_epoch_tasks",
+            "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan"]
 
 
 class SftError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class sft_batch_problem(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("dims", ctypes.POINTER(ctypes.c_int64)),
+                ("R", ctypes.c_int32), ("A", ctypes.POINTER(ctypes.c_void_p)),
+                ("B", ctypes.POINTER(ctypes.c_void_p)), ("C", ctypes.POINTER(ctypes.c_void_p)),
+                ("idx", ctypes.POINTER(ctypes.c_void_p)), ("val", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64), ("lr_A", ctypes.c_float), ("lambda_A", ctypes.c_float),
+                ("lr_B", ctypes.c_float), ("lambda_B", ctypes.c_float)]
 
 
 class sft_config(ctypes.Structure):
@@ -116,6 +129,38 @@ def load(build_if_missing: bool = True):
         i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
         ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
     lib.sft_update_factors_noalloc.restype = ctypes.c_int
+    bp = ctypes.POINTER(sft_batch_problem)
+    lib.sft_batch_workspace_bytes.argtypes = [i32, bp, i64]
+    lib.sft_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.sft_batch_create.argtypes = [i32, bp, i32, i64, i64, i32, vp, ctypes.c_size_t, vp,
+                                     ctypes.POINTER(vp)]
+    lib.sft_batch_create.restype = ctypes.c_int
+    for name in ("sft_batch_refresh", "sft_batch_epoch"):
+        getattr(lib, name).argtypes = [vp]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.sft_batch_loss.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sft_batch_loss.restype = ctypes.c_int
+    lib.sft_batch_snapshot_bytes.argtypes = [vp]
+    lib.sft_batch_snapshot_bytes.restype = ctypes.c_size_t
+    lib.sft_batch_autotune.argtypes = [vp, vp, ctypes.c_size_t, i32, ctypes.POINTER(i64),
+                                       ctypes.POINTER(i32)]
+    lib.sft_batch_autotune.restype = ctypes.c_int
+    lib.sft_batch_sync.argtypes = [vp, i64]
+    lib.sft_batch_sync.restype = ctypes.c_int
+    lib.sft_batch_launch_count.argtypes = [vp]
+    lib.sft_batch_launch_count.restype = i64
+    lib.sft_batch_epoch_tasks.argtypes = [vp]
+    lib.sft_batch_epoch_tasks.restype = i64
+    lib.sft_batch_last_error.argtypes = [vp]
+    lib.sft_batch_last_error.restype = ctypes.c_char_p
+    lib.sft_batch_plan.argtypes = [i32, bp, i32, i64, i32, vp, i64]
+    lib.sft_batch_plan.restype = i64
+    lib.sft_batch_destroy.argtypes = [vp]
+    lib.sft_batch_destroy.restype = None
+    lib.sft_loss_grad_C.argtypes = [ctx, ctypes.POINTER(vp), vp, i64, ctypes.POINTER(vp), i32, vp]
+    lib.sft_loss_grad_C.restype = ctypes.c_int
+    lib.sft_grad_AB.argtypes = [ctx, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.sft_grad_AB.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -298,6 +343,19 @@ def sft_update_factors_noalloc(dims, J, R, mode, A_mode, B_mode, C, idx, val, pe
                                               ctypes.c_void_p(stream)))
 
 
+def sft_loss_grad_C(ctx, idx, val, nnz, dC, accumulate, loss_out: torch.Tensor) -> None:
+    lib = load()
+    dptr = _ptr_array(dC) if dC is not None else None
+    _check(lib, ctx, lib.sft_loss_grad_C(ctx, _ptr_array(idx), _ptr(val), int(nnz), dptr,
+                                         int(accumulate), _ptr(loss_out)), "sft_loss_grad_C")
+
+
+def sft_grad_AB(ctx, dC, scale: Optional[torch.Tensor], gA, gB) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_grad_AB(ctx, _ptr_array(dC), _ptr(scale), _ptr_array(gA),
+                                     _ptr_array(gB)), "sft_grad_AB")
+
+
 class Slices:
     """The slice layout of one mode (device tensors): idx (N int32 arrays),
     val (float32) and row_ptr (I_n + 1 int32), built by sft_group_slices."""
@@ -330,9 +388,17 @@ class Decomposition:
 
     def __init__(self, A0: Sequence[torch.Tensor], B0: Sequence[torch.Tensor],
                  deterministic: bool = True, max_batch: int = 4096, device="cuda",
-                 stream=None, prec: int = SFT_FP32):
-        self.A = [a.to(device=device, dtype=torch.float32).contiguous().clone() for a in A0]
-        self.B = [b.to(device=device, dtype=torch.float32).contiguous().clone() for b in B0]
+                 stream=None, prec: int = SFT_FP32, copy: bool = True):
+        if copy:
+            self.A = [a.to(device=device, dtype=torch.float32).contiguous().clone() for a in A0]
+            self.B = [b.to(device=device, dtype=torch.float32).contiguous().clone() for b in B0]
+        else:
+            # bind the caller's tensors (e.g. nn.Parameters): updates happen in place
+            for t in list(A0) + list(B0):
+                if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("copy=False needs contiguous float32 CUDA tensors")
+            self.A = list(A0)
+            self.B = list(B0)
         self.N = len(self.A)
         self.R = int(self.B[0].shape[1])
         self.dims = [int(a.shape[0]) for a in self.A]
@@ -407,6 +473,282 @@ class Decomposition:
     def sync(self, timeout_ms: int = -1):
         sft_sync(self.ctx, timeout_ms)
 
+    def loss_grad_C(self, idx, val, dC=None, accumulate=False):
+        """Enqueue L = 1/2 sum e^2 and dL/dC^(n) for every mode.  Returns
+        (out, dC): out is a device float64 pair {L, sum |e|}, dC the list of
+        I_n x R float32 gradients (allocated when not given)."""
+        dev = val.device
+        if dC is None:
+            dC = [torch.empty(i, self.R, dtype=torch.float32, device=dev) for i in self.dims]
+        out = torch.empty(2, dtype=torch.float64, device=dev)
+        sft_loss_grad_C(self.ctx, idx, val, val.numel(), dC, accumulate, out)
+        return out, dC
+
+    def grad_AB(self, dC, scale=None):
+        """(gA, gB) = (s dC[n] B[n]^T, s A[n]^T dC[n]) for every mode; s a device
+        float64 scalar tensor or None for 1."""
+        gA = [torch.empty_like(a) for a in self.A]
+        gB = [torch.empty_like(b) for b in self.B]
+        if scale is not None:
+            scale = scale.detach().to(torch.float64).reshape(1).contiguous()
+        sft_grad_AB(self.ctx, dC, scale, gA, gB)
+        return gA, gB
+
     @property
     def launches(self) -> int:
         return sft_launch_count(self.ctx)
+
+
+# ----------------------------------------------------------------------------- autograd
+
+
+class _SampledLossFn(torch.autograd.Function):
+    """L = 1/2 sum_s (x_s - x^_s)^2 as a function of A[0..N) and B[0..N).
+
+    The forward refreshes every C^(n) from the current A and B, then runs the
+    fused loss + dL/dC pass (when any input needs a gradient) and keeps dC for
+    the backward, which projects it onto A and B scaled by the incoming
+    gradient.  All arithmetic runs in libsft's kernels."""
+
+    @staticmethod
+    def forward(fctx, dec, idx, val, *params):
+        N = dec.N
+        for n, t in enumerate(params):
+            own = dec.A[n] if n < N else dec.B[n - N]
+            if t.data_ptr() != own.data_ptr():
+                raise ValueError("parameters are not the tensors bound to the Decomposition")
+        dec.refresh(-1)
+        if any(fctx.needs_input_grad[3:]):
+            out, dC = dec.loss_grad_C(list(idx), val)
+            fctx.dec = dec
+            fctx.dC = dC
+        else:
+            out = torch.empty(2, dtype=torch.float64, device=val.device)
+            sft_loss_grad_C(dec.ctx, list(idx), val, val.numel(), None, 0, out)
+        return out[0]
+
+    @staticmethod
+    def backward(fctx, g):
+        gA, gB = fctx.dec.grad_AB(fctx.dC, g)
+        fctx.dC = None
+        want = fctx.needs_input_grad[3:]
+        N = fctx.dec.N
+        grads = [gA[n] if want[n] else None for n in range(N)]
+        grads += [gB[n] if want[N + n] else None for n in range(N)]
+        return (None, None, None, *grads)
+
+
+class SampledLoss(torch.nn.Module):
+    """Differentiable sampled loss of a sparse FastTucker model.
+
+    Parameters A[n] (I_n x J_n) and B[n] (J_n x R) are ``nn.Parameter``s whose
+    storage is bound to a libsft context, so any torch optimiser can train
+    them; ``forward(idx, val)`` returns L = 1/2 sum over the given nonzeros of
+    (x - x^)^2 as a float64 scalar, and its backward is libsft's gradient
+    (Eq. (10)/(11) without the regulariser, summed over the set)."""
+
+    def __init__(self, A0, B0, prec: int = SFT_FP32, device="cuda"):
+        super().__init__()
+        self.A = torch.nn.ParameterList(
+            [torch.nn.Parameter(a.to(device=device, dtype=torch.float32).contiguous().clone())
+             for a in A0])
+        self.B = torch.nn.ParameterList(
+            [torch.nn.Parameter(b.to(device=device, dtype=torch.float32).contiguous().clone())
+             for b in B0])
+        self.dec = Decomposition([p.data for p in self.A], [p.data for p in self.B], prec=prec,
+                                 device=device, copy=False)
+
+    def forward(self, idx, val):
+        return _SampledLossFn.apply(self.dec, tuple(idx), val, *self.A, *self.B)
+
+
+# ----------------------------------------------------------------------------- batched runner
+
+
+def _bcheck(lib, h, status, what):
+    if status != SFT_OK:
+        msg = lib.sft_batch_last_error(h).decode() if h else ""
+        raise SftError(status, f"{what}: {msg}")
+
+
+def sft_batch_workspace_bytes(probs, min_chunk) -> int:
+    return int(load().sft_batch_workspace_bytes(len(probs), probs, int(min_chunk)))
+
+
+def sft_batch_create(probs, prec, min_chunk, chunk, blocks_per_sm, workspace, stream):
+    lib = load()
+    h = ctypes.c_void_p()
+    st = lib.sft_batch_create(len(probs), probs, int(prec), int(min_chunk), int(chunk),
+                              int(blocks_per_sm), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), ctypes.c_void_p(stream),
+                              ctypes.byref(h))
+    if st != SFT_OK:
+        raise SftError(st, "sft_batch_create")
+    return h
+
+
+def sft_batch_refresh(h) -> None:
+    lib = load()
+    _bcheck(lib, h, lib.sft_batch_refresh(h), "sft_batch_refresh")
+
+
+def sft_batch_epoch(h) -> None:
+    lib = load()
+    _bcheck(lib, h, lib.sft_batch_epoch(h), "sft_batch_epoch")
+
+
+def sft_batch_loss(h, nprob):
+    lib = load()
+    out = (ctypes.c_double * (2 * nprob))()
+    _bcheck(lib, h, lib.sft_batch_loss(h, out), "sft_batch_loss")
+    return [(out[2 * i], out[2 * i + 1]) for i in range(nprob)]
+
+
+def sft_batch_snapshot_bytes(h) -> int:
+    return int(load().sft_batch_snapshot_bytes(h))
+
+
+def sft_batch_autotune(h, scratch: torch.Tensor, epochs: int = 2):
+    lib = load()
+    c, b = ctypes.c_int64(), ctypes.c_int32()
+    _bcheck(lib, h, lib.sft_batch_autotune(h, _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                           int(epochs), ctypes.byref(c), ctypes.byref(b)),
+            "sft_batch_autotune")
+    return int(c.value), int(b.value)
+
+
+def sft_batch_sync(h, timeout_ms: int = -1) -> None:
+    lib = load()
+    _bcheck(lib, h, lib.sft_batch_sync(h, int(timeout_ms)), "sft_batch_sync")
+
+
+def sft_batch_launch_count(h) -> int:
+    return int(load().sft_batch_launch_count(h))
+
+
+def sft_batch_epoch_tasks(h) -> int:
+    return int(load().sft_batch_epoch_tasks(h))
+
+
+def sft_batch_destroy(h) -> None:
+    if h:
+        load().sft_batch_destroy(h)
+
+
+class sft_batch_task_info(ctypes.Structure):
+    _fields_ = [("prob", ctypes.c_int32), ("kind", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("wait", ctypes.c_int32), ("done", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("nslots", ctypes.c_int32), ("pad", ctypes.c_int32), ("begin", ctypes.c_int64),
+                ("end", ctypes.c_int64)]
+
+
+def sft_batch_plan(probs, plan: int, chunk: int, workers: int):
+    """Task list of a plan as a list of dicts (host only)."""
+    lib = load()
+    n = int(lib.sft_batch_plan(len(probs), probs, int(plan), int(chunk), int(workers), None, 0))
+    if n < 0:
+        raise SftError(SFT_EINVAL, "sft_batch_plan")
+    out = (sft_batch_task_info * max(1, n))()
+    lib.sft_batch_plan(len(probs), probs, int(plan), int(chunk), int(workers), out, n)
+    names = [f[0] for f in sft_batch_task_info._fields_]
+    return [{k: getattr(out[i], k) for k in names} for i in range(n)]
+
+
+def batch_problem_records(shapes):
+    """ctypes records for host-side planning: shapes = [(dims, R, nnz)].  The
+    device pointers are dummies (sft_batch_plan never dereferences them)."""
+    arr = (sft_batch_problem * len(shapes))()
+    keep = []
+    for i, (dims, R, nnz) in enumerate(shapes):
+        N = len(dims)
+        d = (ctypes.c_int64 * N)(*dims)
+        fake = (ctypes.c_void_p * N)(*([256] * N))
+        keep += [d, fake]
+        arr[i] = sft_batch_problem(N, d, R, fake, fake, fake, fake, 256, nnz, 0.01, 0.01, 0.01, 0.01)
+    arr._keep = keep
+    return arr
+
+
+class Batch:
+    """Many independent decompositions trained together (include/sft_batch.h).
+
+    problems: sequence of (A0, B0, idx, val): A0[n] (I_n x R), B0[n] (R x R)
+    host or device tensors (copied to float32 device tensors owned here), idx
+    a list of N int32 device tensors and val a float32 device tensor (borrowed;
+    keep them alive).  lr / lam (a number, or one per problem) apply to A and
+    B alike."""
+
+    def __init__(self, problems, prec: int = SFT_FP32, min_chunk: int = 2048, chunk: int = 0,
+                 blocks_per_sm: int = 0, lr: float = 0.01, lam: float = 0.01, device="cuda",
+                 stream=None):
+        self.A, self.B, self.C, self.sets = [], [], [], []
+        cdt = torch.bfloat16 if prec == SFT_BF16 else torch.float32
+        arr = (sft_batch_problem * len(problems))()
+        self._keep = []
+        lrs = list(lr) if isinstance(lr, (list, tuple)) else [lr] * len(problems)
+        lams = list(lam) if isinstance(lam, (list, tuple)) else [lam] * len(problems)
+        for i, (A0, B0, idx, val) in enumerate(problems):
+            A = [a.to(device=device, dtype=torch.float32).contiguous().clone() for a in A0]
+            B = [b.to(device=device, dtype=torch.float32).contiguous().clone() for b in B0]
+            R = int(B[0].shape[1])
+            C = [torch.empty(a.shape[0], R, device=device, dtype=cdt) for a in A]
+            self.A.append(A)
+            self.B.append(B)
+            self.C.append(C)
+            self.sets.append((list(idx), val))
+            dims = (ctypes.c_int64 * len(A))(*[a.shape[0] for a in A])
+            pa, pb, pc, pi = _ptr_array(A), _ptr_array(B), _ptr_array(C), _ptr_array(list(idx))
+            self._keep += [dims, pa, pb, pc, pi]
+            arr[i] = sft_batch_problem(len(A), dims, R, pa, pb, pc, pi, val.data_ptr(), val.numel(),
+                                       lrs[i], lams[i], lrs[i], lams[i])
+        self._probs = arr
+        self.nprob = len(problems)
+        nbytes = sft_batch_workspace_bytes(arr, min_chunk)
+        if nbytes == 0:
+            raise SftError(SFT_EINVAL, "sft_batch_workspace_bytes rejected the problems")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.h = sft_batch_create(arr, prec, min_chunk, chunk, blocks_per_sm, self.workspace,
+                                  stream)
+        sft_batch_refresh(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sft_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refresh(self):
+        sft_batch_refresh(self.h)
+
+    def epoch(self):
+        sft_batch_epoch(self.h)
+
+    def loss(self):
+        """[(sum e^2, sum |e|)] per problem over its own nonzeros."""
+        return sft_batch_loss(self.h, self.nprob)
+
+    def rmse(self):
+        return [(s / max(1, v.numel())) ** 0.5 for (s, _), (_, v) in zip(self.loss(), self.sets)]
+
+    def autotune(self, epochs: int = 2):
+        scratch = torch.empty(max(16, sft_batch_snapshot_bytes(self.h)), dtype=torch.uint8,
+                              device=self.workspace.device)
+        return sft_batch_autotune(self.h, scratch, epochs)
+
+    def sync(self, timeout_ms: int = -1):
+        sft_batch_sync(self.h, timeout_ms)
+
+    @property
+    def launches(self) -> int:
+        return sft_batch_launch_count(self.h)
+
+    @property
+    def epoch_tasks(self) -> int:
+        return sft_batch_epoch_tasks(self.h)

@@ -156,6 +156,33 @@ def spec_order(order: int = 8, dim: int = 10_000, nnz: int = 50_000_000, J: int 
                       noise_sigma=0.05, seed=seed)
 
 
+def spec_batch(count: int = 64, seed: int = 0, dims=(1_000, 200_000), nnz=(10_000, 5_000_000),
+               orders=(3, 6), ranks=(4, 8, 16, 32)) -> List[TensorSpec]:
+    """Independent problems for the batched runner: order uniform in
+    [orders[0], orders[1]], each I_n and nnz log-uniform in the given ranges
+    (nnz at most a quarter of prod I_n), J_n = R drawn from `ranks`, uniform
+    distinct indices, planted model with std(x) ~ 1 (entry std as
+    spec_order) plus N(0, 0.01^2) noise."""
+    out = []
+    for i in range(count):
+        u = uniform(stream_key(seed, 30, i), 12).tolist()
+        N = orders[0] + min(int(u[0] * (orders[1] - orders[0] + 1)), orders[1] - orders[0])
+        R = ranks[min(int(u[1] * len(ranks)), len(ranks) - 1)]
+        lo, hi = math.log(dims[0]), math.log(dims[1])
+        ds = tuple(int(round(math.exp(lo + (hi - lo) * u[2 + k]))) for k in range(N))
+        total = 1
+        for d in ds:
+            total *= d
+        nlo, nhi = math.log(nnz[0]), math.log(nnz[1])
+        nz = int(round(math.exp(nlo + (nhi - nlo) * u[10])))
+        nz = max(1, min(nz, total // 4))
+        sigma = math.sqrt(R ** -0.5 * R ** (-1.0 / (2 * N)))
+        out.append(TensorSpec(f"batch{i}-order{N}-R{R}-{nz}", ds, nz, (R,) * N, R,
+                              ("uniform",) * N, values="planted", planted_sigma=sigma,
+                              noise_sigma=0.01, seed=stream_key(seed, 31, i) & 0x7fffffff))
+    return out
+
+
 def _draw_indices(spec: TensorSpec, n: int, rnd: int, device) -> List[torch.Tensor]:
     out = []
     for k, (I, law) in enumerate(zip(spec.dims, spec.index_law)):

@@ -98,3 +98,52 @@ def rel_fro(got, want):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)
     return float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300))
+
+
+def grad_scale(A, B, idx, val):
+    """Condition bounds of the summed loss gradient: with E_s = |x_s| + x^abs_s
+    (a bound of |e_s|) and |p|_s the product of |C| rows of the other modes,
+      dA[n][i][j] <= sum_{s: i_n(s)=i} E_s (|B^(n)| |p|_s)_j
+      dB[n][j][r] <= sum_s E_s |a^(n)_{i_n(s)}|_j |p|_{s,r}
+    and the loss L = 1/2 sum e^2 moves by at most sum_s E_s x^abs_s per unit
+    of relative rounding."""
+    absC = abs_C(A, B)
+    N = len(A)
+    xh_abs = pred_scale(absC, idx)
+    E = np.abs(val.astype(np.float64)) + xh_abs
+    sA, sB = [], []
+    for n in range(N):
+        p_abs = None
+        for k in range(N):
+            if k == n:
+                continue
+            rows = absC[k][idx[k]]
+            p_abs = rows if p_abs is None else p_abs * rows
+        v_abs = p_abs @ np.abs(B[n]).T
+        out = np.zeros_like(A[n], dtype=np.float64)
+        np.add.at(out, idx[n], E[:, None] * v_abs)
+        sA.append(out)
+        sB.append((np.abs(A[n][idx[n]]) * E[:, None]).T @ p_abs)
+    return sA, sB, float(np.sum(E * xh_abs))
+
+
+def stable_lr(T, cap=0.01, c=0.5):
+    """A learning rate for per-element SGD that stays stable on tensor T at
+    its initial parameters: one step scales a row along v by 1 - lr |v|^2, so
+    lr is kept below c / max_s |v_s|^2 (over every nonzero and mode), and at
+    most `cap`.  The products of N - 1 cached rows are heavy-tailed, so this
+    matters from order 5 or R = 32 on."""
+    A = [a.double() for a in T.A0]
+    B = [b.double() for b in T.B0]
+    C = [a @ b for a, b in zip(A, B)]
+    vmax = 0.0
+    N = len(A)
+    for n in range(N):
+        p = None
+        for k in range(N):
+            if k != n:
+                rows = C[k][T.idx[k].long()]
+                p = rows if p is None else p * rows
+        v = p @ B[n].T
+        vmax = max(vmax, float((v * v).sum(1).max()))
+    return min(cap, c / vmax) if vmax > 0 else cap

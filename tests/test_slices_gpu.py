@@ -8,6 +8,8 @@ that built the layout.  Long slices split into affine maps are forced on with
 small tiles.  The core pass over the layout is compared with the oracle's core
 pass over the same order.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -112,6 +114,86 @@ def test_factor_slices_skewed_tensor(sft, oracle_mod, skewed):
         assert np.all(np.isfinite(got))
         assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n
+
+
+HIGH_ORDER = {
+    # name: (order, dim, nnz, J, lr) -- planted std(x) ~ 1 (synth.spec_order).
+    # Per-element SGD is stable while lr |v|^2 < 2; the products of 7 cached
+    # rows are heavy-tailed (max |v|^2 ~ 6e3 on the order-8 J=32 case), so lr
+    # is chosen under 2 / max |v|^2 (the oracle diverges too above it).
+    "order5_J16": (5, 60, 30_011, 16, 0.002),
+    "order8_J32": (8, 30, 20_003, 32, 1e-4),
+    "order8_J8": (8, 12, 40_000, 8, 0.002),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def high_order_tensor(name):
+    from paper_2210_06014_gb300 import synth
+    order, dim, nnz, J, _ = HIGH_ORDER[name]
+    return synth.make_tensor(synth.spec_order(order, dim, nnz, J, seed=4))
+
+
+@pytest.mark.parametrize("tiling", [(0, 0), (32, 1 << 30)])
+@pytest.mark.parametrize("name", list(HIGH_ORDER))
+def test_high_order_slice_passes(sft, oracle_mod, name, tiling):
+    """Orders 5 and 8 (the 7-other-mode kernels): the element-by-element factor
+    pass of every mode equals the oracle's sequential pass, with the long
+    slices as maps (automatic tiling) or as chains, and a whole-pass core step
+    per mode matches the oracle."""
+    T = high_order_tensor(name)
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    N = len(ix)
+    lr = HIGH_ORDER[name][4]
+    dec = sft.Decomposition(T.A0, T.B0)
+    dec.set_slice_tiling(*tiling)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(N):
+        perm = perm_of(11, 0, 0, n, T.nnz)
+        A0 = dec.A[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, perm.cuda())
+        dec.update_factors_slices(sl, lr=lr, lam=0.01)
+        dec.refresh(n)
+        dec.sync(60_000)
+        ref.factor_pass(n, ix, T.val.numpy(), perm=perm.numpy().astype(np.uint32), batch=1,
+                        lr=lr, lam=0.01)
+        ref.refresh(n)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got)), n
+        # A row takes L = nnz / I_n dependent float32 steps on average; the
+        # slice path re-associates them (maps, products of maps), so its
+        # rounding is bounded by a small multiple of L u (u = 2^-24) relative
+        # to the row, i.e. tol * |A| / |dA| relative to the increment.
+        tol = 4 * (T.nnz / T.spec.dims[n]) * 2.0 ** -24
+        inc = np.linalg.norm(ref.A[n] - A0)
+        assert rel_fro(got, ref.A[n]) < tol, (n, rel_fro(got, ref.A[n]), tol)
+        assert rel_fro(got - A0, ref.A[n] - A0) < tol * np.linalg.norm(ref.A[n]) / inc, n
+    # the core steps start from the same parameters on both sides
+    for n in range(N):
+        dec.A[n].copy_(torch.from_numpy(ref.A[n].astype(np.float32)))
+        ref.A[n] = ref.A[n].astype(np.float32).astype(np.float64)
+    dec.refresh(-1)
+    ref.refresh_all()
+    for n in range(N):
+        B0 = dec.B[n].cpu().numpy().astype(np.float64)
+        A_now = [a.copy() for a in ref.A]
+        B_now = [b.copy() for b in ref.B]
+        sl = dec.slices(n, idx, val, None)
+        dec.update_core_slices(sl, batch=T.nnz, lr=0.5, lam=0.01)
+        dec.refresh(n)
+        dec.sync(60_000)
+        ref.core_pass(n, ix, T.val.numpy(), batch=T.nnz, lr=0.5, lam=0.01)
+        ref.refresh(n)
+        got = dec.B[n].cpu().numpy().astype(np.float64)
+        scale = core_step_scale(A_now, B_now, n, ix, T.val.numpy(), np.arange(T.nnz), 0.5, 0.01)
+        assert_within(got - B0, ref.B[n] - B0, scale + 1e-2 * np.abs(ref.B[n]),
+                      what=f"{name} core step B^({n})")
+        # keep both sides on the same B for the next mode
+        dec.B[n].copy_(torch.from_numpy(ref.B[n].astype(np.float32)))
+        ref.B[n] = ref.B[n].astype(np.float32).astype(np.float64)
+        dec.refresh(n)
+        ref.refresh(n)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2])
