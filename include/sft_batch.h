@@ -107,6 +107,18 @@ sft_status sft_batch_autotune(sft_batch *b, void *scratch, size_t scratch_bytes,
  * reports kernel-flagged errors. */
 sft_status sft_batch_sync(sft_batch *b, int64_t timeout_ms);
 
+/* Polls (of at least 256 ns each) after which a task stops waiting for the
+ * pass it depends on; the kernel then stops and sft_batch_sync reports
+ * SFT_ETIMEOUT.  Default 2^24 (several seconds).  Applies to graphs built
+ * afterwards: call before sft_batch_autotune or re-create.  polls >= 1. */
+sft_status sft_batch_set_wait_limit(sft_batch *b, int64_t polls);
+
+/* Failure injection for tests, done on the host: hold = 1 makes the first
+ * pass of problem `prob` in the epoch list wait for one task more than it
+ * has, so the passes after it can never start and their waits run out (the
+ * kernel stops, SFT_ETIMEOUT); hold = 0 undoes it.  Nothing faults. */
+sft_status sft_batch_hold_pass(sft_batch *b, int32_t prob, int32_t hold);
+
 /* Persistent-kernel launches enqueued so far (one per refresh, epoch, loss). */
 int64_t sft_batch_launch_count(const sft_batch *b);
 

@@ -317,6 +317,9 @@ struct sft_batch {
     Layout L;
     int64_t min_chunk = kMinChunk, chunk = kMinChunk;
     int bps = 1;
+    int64_t wait_limit = kWaitLimit;
+    std::vector<int32_t> epoch_init;   // starting counters of the epoch list (host copy)
+    std::vector<int32_t> epoch_first;  // per problem: counter of its first epoch pass
     BatchArgs args[kPlans] = {};
     cudaGraphExec_t exec[kPlans] = {nullptr, nullptr, nullptr};
     int64_t launches = 0;
@@ -375,7 +378,13 @@ sft_status build_plans(sft_batch *b, int64_t chunk, int bps) {
         g.head = (int32_t *)(b->ws + b->L.head) + pl;
         g.abort = (int32_t *)(b->ws + b->L.abort);
         g.err = (int *)(b->ws + b->L.err);
-        g.wait_limit = kWaitLimit;
+        g.wait_limit = b->wait_limit;
+        if (pl == kPlanEpoch) {
+            b->epoch_init = init;
+            b->epoch_first.assign(b->ps.size(), -1);
+            for (size_t p = 0; p < chains.size(); ++p)
+                if (!chains[p].empty()) b->epoch_first[p] = chains[p][0].counter;
+        }
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(b, e, "graph capture");
@@ -660,6 +669,27 @@ int64_t sft_batch_plan(int32_t nprob, const sft_batch_problem *probs, int32_t pl
     const int64_t n = (int64_t)tasks.size();
     if (out && cap > 0) std::memcpy(out, tasks.data(), (size_t)std::min(n, cap) * sizeof(BatchTask));
     return n;
+}
+
+sft_status sft_batch_set_wait_limit(sft_batch *b, int64_t polls) {
+    if (!b) return SFT_EINVAL;
+    if (polls < 1) return fail(b, SFT_EINVAL, "polls must be >= 1");
+    b->wait_limit = polls;
+    return build_plans(b, b->chunk, b->bps);
+}
+
+sft_status sft_batch_hold_pass(sft_batch *b, int32_t prob, int32_t hold) {
+    if (!b) return SFT_EINVAL;
+    if (prob < 0 || prob >= (int32_t)b->ps.size()) return fail(b, SFT_EINVAL, "prob out of range");
+    const int c = b->epoch_first[prob];
+    if (c < 0) return fail(b, SFT_EINVAL, "problem has no epoch pass");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "stream synchronize");
+    const int32_t v = b->epoch_init[c] + (hold ? 1 : 0);
+    int32_t *di = (int32_t *)(b->ws + b->L.init[kPlanEpoch]);
+    e = cudaMemcpy(di + c, &v, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(b, e, "counter upload");
+    return SFT_OK;
 }
 
 int64_t sft_batch_launch_count(const sft_batch *b) { return b ? b->launches : 0; }

@@ -34,7 +34,8 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_workspace_bytes", "sft_batch_create", "sft_batch_refresh",
             "sft_batch_epoch", "sft_batch_loss", "sft_batch_snapshot_bytes", "sft_batch_autotune",
             "sft_batch_sync", "sft_batch_launch_count", "sft_batch_epoch_tasks",
-            "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan"]
+            "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
+            "sft_batch_set_wait_limit", "sft_batch_hold_pass"]
 
 
 class SftError(RuntimeError):
@@ -153,6 +154,10 @@ def load(build_if_missing: bool = True):
     lib.sft_batch_epoch_tasks.restype = i64
     lib.sft_batch_last_error.argtypes = [vp]
     lib.sft_batch_last_error.restype = ctypes.c_char_p
+    lib.sft_batch_set_wait_limit.argtypes = [vp, i64]
+    lib.sft_batch_set_wait_limit.restype = ctypes.c_int
+    lib.sft_batch_hold_pass.argtypes = [vp, i32, i32]
+    lib.sft_batch_hold_pass.restype = ctypes.c_int
     lib.sft_batch_plan.argtypes = [i32, bp, i32, i64, i32, vp, i64]
     lib.sft_batch_plan.restype = i64
     lib.sft_batch_destroy.argtypes = [vp]
@@ -744,6 +749,16 @@ class Batch:
 
     def sync(self, timeout_ms: int = -1):
         sft_batch_sync(self.h, timeout_ms)
+
+    def set_wait_limit(self, polls: int):
+        lib = load()
+        _bcheck(lib, self.h, lib.sft_batch_set_wait_limit(self.h, int(polls)),
+                "sft_batch_set_wait_limit")
+
+    def hold_pass(self, prob: int, hold: bool = True):
+        lib = load()
+        _bcheck(lib, self.h, lib.sft_batch_hold_pass(self.h, int(prob), 1 if hold else 0),
+                "sft_batch_hold_pass")
 
     @property
     def launches(self) -> int:

@@ -115,3 +115,22 @@ def test_batch_bad_coordinate_is_reported(sft):
     b = sft.Batch(probs)
     with pytest.raises(sft.SftError, match="out of range"):
         b.loss()
+
+
+def test_batch_wait_timeout_is_reported_and_recoverable(sft):
+    """A pass that can never complete (held on the host) makes the tasks after
+    it give up after the poll limit: the epoch reports SFT_ETIMEOUT, and after
+    the hold is lifted the same handle runs epochs normally."""
+    Ts = problems()
+    b = sft.Batch(dev_problems(Ts), lr=[stable_lr(T) for T in Ts])
+    b.set_wait_limit(4000)  # a few ms of polling
+    b.hold_pass(2)
+    b.epoch()
+    with pytest.raises(sft.SftError, match="SFT_ETIMEOUT"):
+        b.sync(60_000)
+    b.hold_pass(2, False)
+    b.set_wait_limit(1 << 24)
+    b.refresh()
+    b.epoch()
+    b.sync(60_000)
+    assert all(np.isfinite(r) for r in b.rmse())
