@@ -55,12 +55,13 @@ def parse():
     p.add_argument("--prec", default="fp32", choices=["fp32", "bf16"],
                    help="storage of the cached products C (arithmetic is float32 either way)")
     p.add_argument("--workload", default="ratings",
-                   choices=["ratings", "order8", "autograd", "batch"],
+                   choices=["ratings", "order8", "autograd", "batch", "sparsity"],
                    help="ratings: 480000x17800x2200, 100M nnz, J=R=16; order8: 8 modes of "
                         "10000, 50M nnz, J=R=32; autograd: loss forward + backward over 4 "
                         "modes of 100000, 20M nnz, J=R=32; batch: 64 independent problems "
                         "(order 3-6, dims 1k-200k, nnz 10k-5M, J=R in 4..32) in one "
-                        "persistent launch per epoch")
+                        "persistent launch per epoch; sparsity: order 3, 1000^3, 20M..100M nnz "
+                        "(2%%..10%% dense), J=R=16, one line with every density")
     p.add_argument("--lr", type=float, default=0.0,
                    help="SGD step for A and B (0 = 0.01 for ratings, 1e-5 for order8)")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
@@ -399,6 +400,75 @@ def run_batch(args, world, rank, lr):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- sparsity
+
+
+def run_sparsity(args, world, rank, lr):
+    """The SGD epoch on order-3 1000^3 tensors with 20M, 40M, ..., 100M nonzeros
+    (Synthetic(Sparsity)); the line's value is the 100M tensor, config.sweep has
+    every density (factor and core time per epoch separately)."""
+    from paper_2210_06014_gb300 import synth
+    metric = "SGD nonzeros/s (factor+core updates)"
+    unit = "nnz/s"
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        T = synth.make_tensor(synth.spec_sparsity(100_000_000),
+                              device="cuda" if torch.cuda.is_available() else "cpu")
+        steps = []
+        for i in range(args.warmup + args.steps):
+            rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4))
+            if i >= args.warmup:
+                steps.append((rate, dt))
+        rate = statistics.median(r for r, _ in steps)
+        print(json.dumps({
+            "impl": "reference", "metric": metric, "value": rate, "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(d for _, d in steps) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "sparsity-1000^3-100M-J16R16", "sample_nnz": S},
+            "cpu_baseline": {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": f"first {S} training nonzeros, one epoch"},
+            "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    from paper_2210_06014_gb300 import sft
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sweep, last = [], None
+    sizes = [20_000_000, 40_000_000, 60_000_000, 80_000_000, 100_000_000]
+    for i, nz in enumerate(sizes):
+        spec = synth.spec_sparsity(nz)
+        t0 = time.perf_counter()
+        T = synth.make_tensor(spec, device=dev)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        final = i == len(sizes) - 1
+        line = run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line=False,
+                       extras=final)
+        if rank == 0:
+            c = line["config"]
+            sweep.append({"nnz": nz, "density": nz / 1e9, "value": line["value"],
+                          "ms_per_step": line["ms_per_step"],
+                          "factor_ms": c["per_step_ms"]["factor"],
+                          "core_ms": c["per_step_ms"]["core"],
+                          "factor_nnz_per_s": c["train_nnz"] * spec.order
+                          / (c["per_step_ms"]["factor"] / 1e3),
+                          "core_nnz_per_s": c["train_nnz"] * spec.order
+                          / (c["per_step_ms"]["core"] / 1e3),
+                          "test_rmse_after": c["test_rmse_after"]})
+            last = line
+        del T
+        torch.cuda.empty_cache()
+    if rank == 0:
+        last["config"]["sweep"] = sweep
+        last["config"]["workload"] = "sparsity-1000^3-20M..100M-J16R16 (value: 100M)"
+        print(json.dumps(last))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- autograd
 
 
@@ -537,6 +607,8 @@ def main():
     elif args.workload == "batch":
         spec = None
         lr = lr or 0.01
+    elif args.workload == "sparsity":
+        return run_sparsity(args, world, rank, lr or 0.01)
     elif args.workload == "autograd":
         spec = synth.spec_order(4, 100_000, args.nnz if args.nnz != 100_000_000 else 20_000_000, 32)
         spec.test_fraction = 0.0
@@ -591,6 +663,22 @@ def main():
     gen_s = time.perf_counter() - t0
     if args.workload == "autograd":
         return run_autograd(args, world, rank, sft, T, spec, metric, unit, gen_s)
+    line = run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line=True,
+            extras=True):
+    """One step = one epoch of Algorithm 2 on tensor T (factor pass + refresh per
+    mode, then core pass + refresh per mode, then the test-set residual sums).
+    Returns the JSON line (rank 0)."""
+    dev = T.val.device
+    workload = spec.name
+    N, J, R = spec.order, spec.J[0], spec.R
+    if not extras:
+        args = argparse.Namespace(**{**vars(args), "no_e2e": True, "no_cpu_baseline": True})
     idx, val = T.idx, T.val
     tidx, tval = T.test_idx, T.test_val
     nnz, ntest = T.nnz, int(tval.numel())
@@ -774,10 +862,10 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        if print_line:
+            print(json.dumps(line))
+        return line
+    return None
 
 
 if __name__ == "__main__":

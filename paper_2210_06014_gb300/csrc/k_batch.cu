@@ -60,27 +60,36 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     return v;
 }
 
-// Coordinates of nonzero s, checked against the mode lengths; `in` receives
-// the coordinate of mode n (no runtime indexing of ik, which would put it in
-// local memory).
-__device__ __forceinline__ bool load_coords_b(const BatchProblem &P, int64_t s, bool ok, int n,
-                                              int32_t (&ik)[kBatchMaxOrder], int32_t &in,
-                                              int *err) {
-    in = 0;
+// Coordinates and value of the nonzero a lane group visits next, loaded one
+// iteration ahead of use (raw); take() checks them and hands them over.
+struct NextSample {
+    int32_t ik[kBatchMaxOrder];
+    float x;
+    __device__ __forceinline__ void fetch(const BatchProblem &P, int64_t s, int64_t end) {
+        const bool in = s < end;
 #pragma unroll
-    for (int k = 0; k < kBatchMaxOrder; ++k) {
-        ik[k] = 0;
-        if (ok && k < P.N) {
-            ik[k] = __ldg(P.idx[k] + s);
-            if ((uint32_t)ik[k] >= (uint32_t)P.dims[k]) {
-                atomicOr(err, kErrIndex);
-                ok = false;
-            }
-            if (k == n) in = ik[k];
-        }
+        for (int k = 0; k < kBatchMaxOrder; ++k) ik[k] = (in && k < P.N) ? __ldg(P.idx[k] + s) : 0;
+        x = in ? __ldg(P.val + s) : 0.f;
     }
-    return ok;
-}
+    __device__ __forceinline__ bool take(const BatchProblem &P, bool ok, int n,
+                                         int32_t (&out)[kBatchMaxOrder], int32_t &in, float &xo,
+                                         int *err) const {
+        in = 0;
+#pragma unroll
+        for (int k = 0; k < kBatchMaxOrder; ++k) {
+            out[k] = ik[k];
+            if (ok && k < P.N) {
+                if ((uint32_t)ik[k] >= (uint32_t)P.dims[k]) {
+                    atomicOr(err, kErrIndex);
+                    ok = false;
+                }
+                if (k == n) in = ik[k];
+            }
+        }
+        xo = ok ? x : 0.f;
+        return ok;
+    }
+};
 
 // Lane's 4 entries of prod_{k != skip} C^(k)[i_k] (skip = -1: every mode).
 template <int R, typename CT>
@@ -131,11 +140,14 @@ __device__ void task_factor(const BatchProblem &P, const BatchTask &tk, float *s
     const int sub = lane & (T - 1), gw = lane / T;
     const int n = tk.mode;
     float *An = P.A[n];
+    NextSample nxt;
+    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
     for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
         const int64_t s = t0 + gw;
         int32_t ik[kBatchMaxOrder], in;
-        const bool ok = load_coords_b(P, s, s < tk.end, n, ik, in, err);
-        const float x = ok ? __ldg(P.val + s) : 0.f;
+        float x;
+        const bool ok = nxt.take(P, s < tk.end, n, ik, in, x, err);
+        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
         const float4 p = gather_product<R, CT>(P, ik, ok, n, sub);
         float *arow = An + (int64_t)in * R + 4 * sub;
         const float4 a = ok ? __ldcg(reinterpret_cast<const float4 *>(arow))
@@ -199,11 +211,14 @@ __device__ void task_core(const BatchProblem &P, const BatchTask &tk, float *sB,
 #pragma unroll
     for (int q = 0; q < EPL; ++q) acc[q] = tot[q] = 0.f;
     int fold = 0;
+    NextSample nxt;
+    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
     for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
         const int64_t s = t0 + gw;
         int32_t ik[kBatchMaxOrder], in;
-        const bool ok = load_coords_b(P, s, s < tk.end, n, ik, in, err);
-        const float x = ok ? __ldg(P.val + s) : 0.f;
+        float x;
+        const bool ok = nxt.take(P, s < tk.end, n, ik, in, x, err);
+        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
         const float4 p = gather_product<R, CT>(P, ik, ok, n, sub);
         const float4 a = ok ? __ldcg(reinterpret_cast<const float4 *>(P.A[n] + (int64_t)in * R) + sub)
                             : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -266,11 +281,14 @@ __device__ void task_loss(const BatchProblem &P, const BatchTask &tk, double *sr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (T - 1), gw = lane / T;
     double s2 = 0.0, s1 = 0.0;
+    NextSample nxt;
+    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
     for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
         const int64_t s = t0 + gw;
         int32_t ik[kBatchMaxOrder], in;
-        const bool ok = load_coords_b(P, s, s < tk.end, -1, ik, in, err);
-        const float x = ok ? __ldg(P.val + s) : 0.f;
+        float x;
+        const bool ok = nxt.take(P, s < tk.end, -1, ik, in, x, err);
+        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
         const float4 p = gather_product<R, CT>(P, ik, ok, -1, sub);
         const float xh = group_sum<T>((p.x + p.y) + (p.z + p.w));
         if (ok && sub == 0) {

@@ -56,22 +56,31 @@ __global__ void __launch_bounds__(kGradThreads) k_loss_grad(PassArgs a, GradBufs
     const int64_t p0 = (int64_t)blockIdx.x * span;
     const int64_t p1 = min(a.count, p0 + span);
     double s2 = 0.0, s1 = 0.0;
+    // The coordinates and value of the next nonzero are loaded one iteration
+    // ahead (raw, checked when used), so only the row gathers wait on memory.
+    int32_t nik[NB];
+    float nx = 0.f;
+    auto fetch = [&](int64_t s) {
+        const bool in = s < p1;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) nik[k] = (in && k < a.N) ? __ldg(a.idx[k] + s) : 0;
+        nx = in ? __ldg(a.val + s) : 0.f;
+    };
+    fetch(p0 + (int64_t)warp * GPW + gw);
     for (int64_t t0 = p0 + (int64_t)warp * GPW; t0 < p1; t0 += (int64_t)WARPS * GPW) {
         const int64_t s = t0 + gw;
         bool ok = s < p1;
         int32_t ik[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            ik[k] = 0;
-            if (ok && k < a.N) {
-                ik[k] = __ldg(a.idx[k] + s);
-                if ((uint32_t)ik[k] >= (uint32_t)a.dims[k]) {
-                    atomicOr(a.err, kErrIndex);
-                    ok = false;
-                }
+            ik[k] = nik[k];
+            if (ok && k < a.N && (uint32_t)ik[k] >= (uint32_t)a.dims[k]) {
+                atomicOr(a.err, kErrIndex);
+                ok = false;
             }
         }
-        const float x = ok ? __ldg(a.val + s) : 0.f;
+        const float x = ok ? nx : 0.f;
+        fetch(s + (int64_t)WARPS * GPW);
         float4 c[NB], pre[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k)

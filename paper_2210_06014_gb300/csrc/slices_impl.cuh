@@ -137,6 +137,20 @@ __device__ __forceinline__ bool slice_ok(const SliceArgs &g, int64_t s, int64_t 
     return 0 <= s && s < e && e <= g.a.nnz;
 }
 
+template <int L>
+__device__ __forceinline__ void store_run(float *p, const float (&r)[L]) {
+    if constexpr (L >= 4) {
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q)
+            *reinterpret_cast<float4 *>(p + 4 * q) =
+                make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    } else if constexpr (L == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
+    } else {
+        p[0] = r[0];
+    }
+}
+
 // ============================================================================ factor: direct run
 // Runs positions [s0, s1) of slice r element by element.  The lane holds the
 // JL entries [sub*JL, (sub+1)*JL) of a_r.  The next position's coordinates and
@@ -150,6 +164,22 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
     float av[JL];
     float *arow = a.A + (int64_t)r * J + sub * JL;
     load_run<JL>(arow, av);
+    // One-step software pipeline: v of position t does not depend on the row,
+    // so it is computed while the row update of position t-1 (which needs the
+    // row) is still in flight; the pending step is applied in the next call.
+    float vq[JL];
+    float xq = 0.f;
+    bool okq = false, have = false;
+    auto apply = [&]() {
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vq[q], dot);
+        const float e = xq - group_sum_m<T>(dot, m);
+        if (okq) {
+#pragma unroll
+            for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
+        }
+    };
     walk<NB, R, CT, 4, false>(a, s0, s1, sub, [&](int32_t, float x, bool ok, const float4 &p) {
         float vp[J];
 #pragma unroll
@@ -158,24 +188,15 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
             vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
         }
         group_reduce_scatter_m<T, J>(vp, sub, m);
-        float dot = 0.f;
+        if (have) apply();
 #pragma unroll
-        for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vp[q], dot);
-        const float e = x - group_sum_m<T>(dot, m);
-        if (ok) {
-#pragma unroll
-            for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vp[q] - a.lam * av[q]);
-        }
+        for (int q = 0; q < JL; ++q) vq[q] = vp[q];
+        xq = x;
+        okq = ok;
+        have = true;
     });
-    if constexpr (JL >= 4) {
-#pragma unroll
-        for (int q = 0; q < JL / 4; ++q)
-            *reinterpret_cast<float4 *>(arow + 4 * q) =
-                make_float4(av[4 * q], av[4 * q + 1], av[4 * q + 2], av[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < JL; ++q) arow[q] = av[q];
-    }
+    if (have) apply();
+    store_run<JL>(arow, av);
 }
 
 // Finds the crossing slice whose first tile boundary is b (1 <= b < ntiles).
@@ -193,20 +214,6 @@ __device__ __forceinline__ bool first_boundary_slice(const SliceArgs &g, int64_t
         return false;
     }
     return s / g.W + 1 == b;
-}
-
-template <int L>
-__device__ __forceinline__ void store_run(float *p, const float (&r)[L]) {
-    if constexpr (L >= 4) {
-#pragma unroll
-        for (int q = 0; q < L / 4; ++q)
-            *reinterpret_cast<float4 *>(p + 4 * q) =
-                make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    } else if constexpr (L == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
-    } else {
-        p[0] = r[0];
-    }
 }
 
 constexpr int kSliceThreads = 256;
@@ -342,7 +349,43 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         pw = ainv;
         since = 0;
     };
-    walk<NB, R, CT, 2, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
+    // One-step software pipeline: v of position t (independent of M) is
+    // computed while the rank-1 update of position t-1 is applied.
+    float vq[JL];
+    float xq = 0.f;
+    bool okq = false, have = false;
+    auto apply = [&]() {
+        // w = v^T M' (all J columns), s = v . c'
+        float w[J];
+#pragma unroll
+        for (int k = 0; k < J; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < JL; ++q) acc = fmaf(vq[q], M[q][k], acc);
+            w[k] = acc;
+        }
+        float sc = 0.f;
+#pragma unroll
+        for (int q = 0; q < JL; ++q) sc = fmaf(vq[q], cv[q], sc);
+#pragma unroll
+        for (int k = 0; k < J; ++k) w[k] = group_sum_m<T>(w[k], m);
+        sc = group_sum_m<T>(sc, m);
+        if (okq) {
+            const float xs = a.lr * xq * pw;
+#pragma unroll
+            for (int q = 0; q < JL; ++q) {
+                const float nv = nvc * vq[q];
+#pragma unroll
+                for (int k = 0; k < J; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
+                cv[q] = fmaf(xs, vq[q], fmaf(nv, sc, cv[q]));
+            }
+            apow *= alpha;
+            pw *= ainv;
+            if (++since == 16) fold();
+        }
+    };
+    // prefetch depth 1: with the pipelined step a deeper ring spills (measured)
+    walk<NB, R, CT, 1, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
         float v[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -350,42 +393,18 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
             v[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
         }
         group_reduce_scatter_m<T, J>(v, sub, m);  // v[0..JL): the lane's slice of v
-        // w = v^T M' (all J columns), s = v . c'
-        float w[J];
+        if (have) apply();
 #pragma unroll
-        for (int k = 0; k < J; ++k) {
-            float acc = 0.f;
-#pragma unroll
-            for (int q = 0; q < JL; ++q) acc = fmaf(v[q], M[q][k], acc);
-            w[k] = acc;
-        }
-        float sc = 0.f;
-#pragma unroll
-        for (int q = 0; q < JL; ++q) sc = fmaf(v[q], cv[q], sc);
-#pragma unroll
-        for (int k = 0; k < J; ++k) w[k] = group_sum_m<T>(w[k], m);
-        sc = group_sum_m<T>(sc, m);
-        if (ok0) {
-            const float xs = a.lr * x0 * pw;
-#pragma unroll
-            for (int q = 0; q < JL; ++q) {
-                const float nv = nvc * v[q];
-#pragma unroll
-                for (int k = 0; k < J; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
-                cv[q] = fmaf(xs, v[q], fmaf(nv, sc, cv[q]));
-            }
-            apow *= alpha;
-            pw *= ainv;
-            if (++since == 16) fold();
-        }
+        for (int q = 0; q < JL; ++q) vq[q] = v[q];
+        xq = x0;
+        okq = ok0;
+        have = true;
     });
+    if (have) apply();
     fold();
 #pragma unroll
-    for (int q = 0; q < JL; ++q) {
-#pragma unroll
-        for (int k = 0; k < J; ++k) out[(sub * JL + q) * J + k] = M[q][k];
-        out[J * J + sub * JL + q] = cv[q];
-    }
+    for (int q = 0; q < JL; ++q) store_run<J>(out + (sub * JL + q) * J, M[q]);
+    store_run<JL>(out + J * J + sub * JL, cv);
 }
 
 // One group per tile: maps for the tile's first run (if its slice started

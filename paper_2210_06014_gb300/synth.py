@@ -156,6 +156,16 @@ def spec_order(order: int = 8, dim: int = 10_000, nnz: int = 50_000_000, J: int 
                       noise_sigma=0.05, seed=seed)
 
 
+def spec_sparsity(nnz: int, seed: int = 0, dim: int = 1000, J: int = 16) -> TensorSpec:
+    """Synthetic(Sparsity)-style tensor: order 3, every mode `dim` long, `nnz`
+    distinct uniform nonzeros (20M..100M at dim 1000 is 2%..10% dense), integer
+    values 1-5 from a standardised planted J=R model, 90/10 split, init as the
+    ratings tensor."""
+    return TensorSpec(f"sparsity-{dim}^3-{nnz}-J{J}R{J}", (dim,) * 3, nnz, (J,) * 3, J,
+                      ("uniform",) * 3, values="ratings", planted_sigma=0.3, noise_sigma=0.0,
+                      test_fraction=0.1, init="uniform_mean", seed=seed)
+
+
 def spec_batch(count: int = 64, seed: int = 0, dims=(1_000, 200_000), nnz=(10_000, 5_000_000),
                orders=(3, 6), ranks=(4, 8, 16, 32)) -> List[TensorSpec]:
     """Independent problems for the batched runner: order uniform in
