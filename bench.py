@@ -64,6 +64,9 @@ def parse():
                         "(2%%..10%% dense), J=R=16, one line with every density")
     p.add_argument("--lr", type=float, default=0.0,
                    help="SGD step for A and B (0 = 0.01 for ratings, 1e-5 for order8)")
+    p.add_argument("--fibers", default="auto", choices=["auto", "on", "off"],
+                   help="form v once per fiber (tuple of the other modes' coordinates) in the "
+                        "factor pass: on, off, or auto = for modes with at most nnz/2 fibers")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
     p.add_argument("--slice-max-direct", type=int, default=0,
                    help="longest crossing slice run element by element (0 = automatic)")
@@ -701,6 +704,19 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             sl._scratch = None  # sort keys are no longer needed
         touched = [int((sl.row_ptr[1:] > sl.row_ptr[:-1]).sum()) for sl in slices]
         rows_per_nnz = sum(touched) / (N * nnz)
+        if args.fibers != "off":
+            t0 = time.perf_counter()
+            for sl in slices:
+                try:
+                    nf = sl.build_fibers(dec)
+                except sft.SftError:  # fiber key does not fit 64 bits
+                    continue
+                if args.fibers == "auto" and nf > nnz // 2:
+                    sl.drop_fibers()
+            torch.cuda.synchronize()
+            layout_s += time.perf_counter() - t0
+    fibers = [{"mode": n, "fibers": sl.nfibers if sl.fid is not None else None,
+               "used": sl.fid is not None} for n, sl in enumerate(slices)]
 
     ev = {}
 
@@ -785,11 +801,22 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     c_ms, c_step = avg_ms("core", N)
     r_ms, r_step = avg_ms("refresh", 2 * N)
     l_ms, l_step = avg_ms("loss", 1)
-    fac_bytes, core_bytes = algorithmic_bytes(N, J, R, args.path, rows_per_nnz,
-                                              2 if args.prec == "bf16" else 4)
+    c_bytes = 2 if args.prec == "bf16" else 4
+    fac_bytes, core_bytes = algorithmic_bytes(N, J, R, args.path, rows_per_nnz, c_bytes)
+    # factor bytes of one epoch, mode by mode: a mode with fibers reads its
+    # fiber id and v (J floats) per nonzero instead of the N-1 cached rows, and
+    # first forms v per fiber (N-1 coordinates and rows in, J floats out)
+    fac_epoch = 0.0
+    for fb in fibers or [{"used": False}] * N:
+        if fb["used"]:
+            nf = fb["fibers"]
+            fac_epoch += nnz * (fac_bytes - (N - 1) * R * c_bytes - 4 * (N - 1) + 4 + J * 4)
+            fac_epoch += nf * (4 * (N - 1) + (N - 1) * R * c_bytes + J * 4 + 4)
+        else:
+            fac_epoch += nnz * fac_bytes
     peak, peak_kind = peaks()
     kernels = {
-        "factor": (f_ms, fac_bytes * nnz / (f_ms / 1e3) / 1e9),
+        "factor": (f_ms, fac_epoch / N / (f_ms / 1e3) / 1e9),
         "core": (c_ms, core_bytes * nnz / (c_ms / 1e3) / 1e9),
     }
     dom = "factor" if f_step >= c_step else "core"
@@ -802,6 +829,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     if not args.no_e2e:
         if slices:
             dev_in = [t for sl in slices for t in sl.idx + [sl.val, sl.row_ptr]]
+            dev_in += [t for sl in slices if sl.fid is not None for t in (sl.fid, sl.frep)]
         else:
             dev_in = list(idx) + [val]
         dev_in += list(tidx) + [tval]
@@ -846,12 +874,14 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                               "after every pass; test loss",
                 "layout_build_s": round(layout_s, 3),
                 "factor_rows_per_nnz": rows_per_nnz,
+                "fibers": fibers,
                 "l2": "inputs larger than L2 (COO 1.6 GB)", "generation_s": round(gen_s, 2),
                 "test_rmse_after": test_rmse,
                 "per_launch_ms": {"factor": f_ms, "core": c_ms, "refresh": r_ms, "loss": l_ms},
                 "per_step_ms": {"factor": f_step, "core": c_step, "refresh": r_step,
                                 "loss": l_step},
-                "algorithmic_bytes_per_nnz": {"factor": fac_bytes, "core": core_bytes},
+                "algorithmic_bytes_per_nnz": {"factor": fac_epoch / (N * nnz),
+                                              "core": core_bytes},
                 "achieved_gbs": {k: v[1] for k, v in kernels.items()},
             },
             "roofline": {"bound": "hbm", "kernel": f"{dom} pass", "achieved": ach, "peak": peak,

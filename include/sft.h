@@ -231,6 +231,40 @@ sft_status sft_update_core_slices(sft_ctx *ctx, int32_t mode, const int32_t *con
                                   const float *sval, const int32_t *row_ptr, int64_t nnz,
                                   int64_t batch, float lr, float lambda);
 
+/* ---------------------------------------------------------------------------
+ * Fibers: the shared intermediate variables of Section "Reusable Intermediate
+ * Variables" (Eq. (12)-(13)).  A fiber of mode n is a tuple (i_k)_{k != n};
+ * its nonzeros share p = prod_{k != n} C^(k)[i_k] and v = B^(n) p.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device scratch sft_group_fibers needs (a hash table of at least
+ * twice nnz slots, 16 bytes each). */
+size_t sft_fibers_scratch_bytes(int64_t nnz);
+
+/* For the slice layout of mode n (sidx: N device pointers from
+ * sft_group_slices), writes fid[pos] (DEVICE int32, nnz entries) = the fiber of
+ * each position, numbered 0..nfibers-1, and frep[f] (DEVICE int32, room for
+ * nnz entries) = one position of fiber f; *nfibers (HOST) receives the count.
+ * The numbering depends on thread scheduling; the fibers themselves do not.
+ * Synchronises the stream.  SFT_ENOTSUP if the product of the other modes'
+ * lengths is 4e18 or more (the fiber key is their exact linear index).
+ * Coordinates out of range get fid -1 and are reported as SFT_EINVAL. */
+sft_status sft_group_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx, int64_t nnz,
+                            int32_t *fid, int32_t *frep, int64_t *nfibers, void *scratch,
+                            size_t scratch_bytes);
+
+/* sft_update_factors_slices with v formed once per fiber: first
+ * V[f][0..J_n) = B^(n) p_f for every fiber (V: DEVICE float32, nfibers x J_n,
+ * 16-byte aligned, caller-owned), then the element-by-element slice pass reads
+ * v from V.  fid / frep / nfibers from sft_group_fibers on the same layout.
+ * v is formed with the same operations in the same order as the per-nonzero
+ * path, so the result is the same.  Enqueues only. */
+sft_status sft_update_factors_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
+                                     const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                     const int32_t *fid, const int32_t *frep, int64_t nfibers,
+                                     float *V, float lr, float lambda, void *workspace,
+                                     size_t workspace_bytes);
+
 /* Tiling of the slice passes: tile = positions per work item (0 = automatic),
  * max_direct = longest slice that crosses a tile boundary and is still run
  * element by element by one lane group (0 = automatic, < 0 = none: every

@@ -1,0 +1,263 @@
+// k_fibers.cu -- fibers of a slice layout and their shared vectors, the
+// "shared intermediate variables" of cuFasterTucker (Section "Reusable
+// Intermediate Variables", Eq. (12)-(13)).
+//
+// For mode n a fiber is a tuple (i_k)_{k != n}.  All nonzeros of one fiber
+// share p = prod_{k != n} C^(k)[i_k] and v = B^(n) p, and during a factor pass
+// over mode n neither C^(k != n) nor B^(n) changes, so v can be formed once
+// per fiber at the start of the pass instead of once per nonzero.
+//
+// Fiber ids (layout time): the exact 64-bit linear key of the tuple is
+// inserted into an open-addressing table (atomicCAS, linear probing, bounded
+// by the table size, which is at least twice the number of nonzeros); the
+// occupied slots are then numbered by an atomic counter.  Ids therefore depend
+// on scheduling, but each fiber's v does not, so results are reproducible.
+//
+// Per pass: k_fiber_v forms every fiber's v with the same arithmetic, in the
+// same order, as the per-nonzero path (product of the other modes' rows in
+// ascending mode order, partial products with B over the lane's r, group
+// reduce-scatter), so the fiber path gives the same bits.
+#include "slices_impl.cuh"
+
+namespace sft {
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kFibThreads = 256;
+
+__device__ __forceinline__ unsigned long long mix_key(unsigned long long z) {
+    // SplitMix64 finaliser (Steele, Lea, Flood 2014), used only to spread keys
+    z ^= z >> 30;
+    z *= 0xbf58476d1ce4e5b9ull;
+    z ^= z >> 27;
+    z *= 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return z;
+}
+
+struct FiberKeyArgs {
+    const int32_t *oidx[kMaxOrder];
+    int32_t odims[kMaxOrder];
+    unsigned long long stride[kMaxOrder];
+    int no;  // number of other modes
+};
+
+__global__ void k_fiber_clear(unsigned long long *table, int64_t cap) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (int64_t)gridDim.x * blockDim.x)
+        table[i] = kEmpty;
+}
+
+// slot_of[t] = table slot of position t's fiber (-1 for bad coordinates);
+// the first position to claim a slot is recorded as the fiber's representative.
+__global__ void k_fiber_insert(FiberKeyArgs f, int64_t nnz, unsigned long long *table,
+                               int32_t *slot_pos, int64_t cap, int32_t *slot_of, int *err) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = 0;
+        bool ok = true;
+        for (int q = 0; q < f.no; ++q) {
+            const int32_t i = f.oidx[q][t];
+            if ((uint32_t)i >= (uint32_t)f.odims[q]) ok = false;
+            else key += (unsigned long long)i * f.stride[q];
+        }
+        if (!ok) {
+            atomicOr(err, kErrIndex);
+            slot_of[t] = -1;
+            continue;
+        }
+        int64_t h = (int64_t)(mix_key(key) & (unsigned long long)(cap - 1));
+        int32_t slot = -1;
+        for (int64_t probe = 0; probe < cap; ++probe) {
+            const unsigned long long prev = atomicCAS(table + h, kEmpty, key);
+            if (prev == kEmpty) {
+                slot_pos[h] = (int32_t)t;
+                slot = (int32_t)h;
+                break;
+            }
+            if (prev == key) {
+                slot = (int32_t)h;
+                break;
+            }
+            h = (h + 1) & (cap - 1);
+        }
+        if (slot < 0) atomicOr(err, kErrIndex);  // unreachable: cap >= 2 nnz
+        slot_of[t] = slot;
+    }
+}
+
+__global__ void k_fiber_number(const unsigned long long *table, const int32_t *slot_pos,
+                               int64_t cap, int32_t *slot_fid, int32_t *frep,
+                               unsigned long long *count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (table[i] == kEmpty) continue;
+        const unsigned long long id = atomicAdd(count, 1ull);
+        slot_fid[i] = (int32_t)id;
+        frep[id] = slot_pos[i];
+    }
+}
+
+__global__ void k_fiber_remap(int32_t *fid, int64_t nnz, const int32_t *slot_fid) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = fid[t];
+        fid[t] = s >= 0 ? slot_fid[s] : -1;
+    }
+}
+
+// V[f] = B^(n) prod_{k != n} C^(k)[i_k(f)] for every fiber; T = R/4 lanes per
+// fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  The coordinates come
+// from the fiber's representative position in the slice layout.
+template <int R, int J, typename CT>
+__global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, const int32_t *frep,
+                                                         int64_t nfibers, float *V) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int NO = kMaxOrder - 1;
+    __shared__ __align__(16) float sB[J * R];
+    for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = a.B[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const int64_t stride = (int64_t)gridDim.x * (kFibThreads / T);
+    // every group of a warp runs the same number of iterations (full-mask shuffles)
+    const int64_t first = (int64_t)blockIdx.x * (kFibThreads / T) + threadIdx.x / T;
+    const int64_t warp_first = first - (lane / T);
+    for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
+        const int64_t f = f0 + lane / T;
+        bool ok = f < nfibers;
+        int64_t pos = 0;
+        if (ok) {
+            pos = __ldg(frep + f);
+            if (pos < 0 || pos >= a.nnz) {
+                atomicOr(a.err, kErrIndex);
+                ok = false;
+            }
+        }
+        Rows<NO> w;
+#pragma unroll
+        for (int q = 0; q < NO; ++q) {
+            w.r[q] = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (ok && q < a.N - 1) {
+                const int32_t i = __ldg(a.oidx[q] + pos);
+                if ((uint32_t)i < (uint32_t)a.odims[q]) w.r[q] = ldC<CT>(a.oC[q], (int64_t)i * R + 4 * sub);
+            }
+        }
+        const float4 p = product<NO>(w);
+        float vp[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+            vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
+        }
+        group_reduce_scatter<T, J>(vp, sub);
+        float vq[JL];
+#pragma unroll
+        for (int q = 0; q < JL; ++q) vq[q] = vp[q];
+        if (ok) store_run<JL>(V + f * J + sub * JL, vq);
+    }
+}
+
+}  // namespace
+
+int64_t fiber_table_capacity(int64_t nnz) {
+    int64_t cap = 1024;
+    while (cap < 2 * nnz) cap <<= 1;
+    return cap;
+}
+
+cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, void *scratch,
+                                int64_t *nfibers, cudaStream_t st, int sms, int64_t *launches) {
+    const int64_t cap = fiber_table_capacity(a.nnz);
+    char *p = (char *)scratch;
+    unsigned long long *table = (unsigned long long *)p;
+    p += cap * sizeof(unsigned long long);
+    int32_t *slot_pos = (int32_t *)p;
+    p += cap * sizeof(int32_t);
+    int32_t *slot_fid = (int32_t *)p;
+    p += cap * sizeof(int32_t);
+    unsigned long long *count = (unsigned long long *)p;
+    FiberKeyArgs f{};
+    f.no = a.N - 1;
+    unsigned long long s = 1;
+    for (int q = f.no - 1; q >= 0; --q) {
+        f.oidx[q] = a.oidx[q];
+        f.odims[q] = a.odims[q];
+        f.stride[q] = s;
+        s *= (unsigned long long)a.odims[q];
+    }
+    const int blocks = sms * 8;
+    k_fiber_clear<<<blocks, kFibThreads, 0, st>>>(table, cap);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_fiber_insert<<<blocks, kFibThreads, 0, st>>>(f, a.nnz, table, slot_pos, cap, fid, a.err);
+    k_fiber_number<<<blocks, kFibThreads, 0, st>>>(table, slot_pos, cap, slot_fid, frep, count);
+    k_fiber_remap<<<blocks, kFibThreads, 0, st>>>(fid, a.nnz, slot_fid);
+    *launches += 4;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *nfibers = (int64_t)h;
+    return e;
+}
+
+cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
+                                 float *maps, const int32_t *fid, const int32_t *frep,
+                                 int64_t nfibers, float *V, int J, int R, const SliceStreams &ss_in,
+                                 int sms, int64_t *launches) {
+    SliceStreams ss = ss_in;
+    const cudaStream_t st = ss.tiles;
+    // 1. v of every fiber
+    if (nfibers > 0) {
+        const int64_t per_block = kFibThreads / (R / 4);
+        int64_t blocks = (nfibers + per_block - 1) / per_block;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        if (a.cbf16)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16><<<(int)blocks, kFibThreads, 0, st>>>(a, frep, nfibers, V)));
+        else
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float><<<(int)blocks, kFibThreads, 0, st>>>(a, frep, nfibers, V)));
+        *launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // 2. the slice factor pass reading v from the table
+    const bool fork = ss.fork && ss.chains_done && ss.maps_done && ss.chains && ss.maps &&
+                      ss.chains != st && ss.maps != st;
+    if (fork) {
+        cudaEventRecord(ss.fork, st);
+        cudaStreamWaitEvent(ss.chains, ss.fork, 0);
+        cudaStreamWaitEvent(ss.maps, ss.fork, 0);
+    } else {
+        ss.chains = ss.maps = st;
+    }
+    SliceArgs g{};
+    g.a = a;
+    g.row_ptr = row_ptr;
+    g.W = W;
+    g.Lseq = Lseq;
+    g.ntiles = (a.nnz + W - 1) / W;
+    g.maps = maps;
+    g.fid = fid;
+    g.V = V;
+    g.nfibers = nfibers;
+    const bool with_maps = maps != nullptr;
+    factor_slices_fv(g, R, J, with_maps, ss, sms, launches);
+    if (fork) {
+        cudaEventRecord(ss.chains_done, ss.chains);
+        cudaEventRecord(ss.maps_done, ss.maps);
+        cudaStreamWaitEvent(st, ss.chains_done, 0);
+        cudaStreamWaitEvent(st, ss.maps_done, 0);
+    }
+    if (with_maps && g.ntiles > 1) {
+        cudaError_t e = launch_slice_combine(g, J, R, st, sms);
+        *launches += 2;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sft

@@ -6,7 +6,7 @@ namespace sft {
 void factor_slices_no15_bf16(const SliceArgs &g, int R, int J, bool with_maps,
                               const SliceStreams &ss, int sms, int64_t *launches) {
     dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-        factor_slices_t<15, decltype(r_c)::value, decltype(j_c)::value, __nv_bfloat16>(g, with_maps, ss,
+        factor_slices_t<false, 15, decltype(r_c)::value, decltype(j_c)::value, __nv_bfloat16>(g, with_maps, ss,
                                                                               sms, launches);
     });
 }

@@ -406,17 +406,25 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
         cudaStreamWaitEvent(st, ss.maps_done, 0);
     }
     if (with_maps && g.ntiles > 1) {
-        dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-            constexpr int R_ = decltype(r_c)::value, J_ = decltype(j_c)::value;
-            const int gpb = kSliceThreads / (R_ / 4);
-            const int cth = kComposeGroups * (R_ / 4);
-            const int gc = grid_for(k_slices_compose<R_, J_>, cth, 0, kComposeGroups, g.ntiles, sms);
-            k_slices_compose<R_, J_><<<gc, cth, 0, st>>>(g);
-            const int gb = grid_for(k_slices_combine<R_, J_>, kSliceThreads, 0, gpb, g.ntiles, sms);
-            k_slices_combine<R_, J_><<<gb, kSliceThreads, 0, st>>>(g);
-        });
+        cudaError_t e = launch_slice_combine(g, J, R, st, sms);
         *launches += 2;
+        if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+// Compose the piece maps of long slices in blocks, then apply them in order
+// to the rows (after the map kernel has finished).
+cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms) {
+    dispatch_rj(R, J, [&](auto r_c, auto j_c) {
+        constexpr int R_ = decltype(r_c)::value, J_ = decltype(j_c)::value;
+        const int gpb = kSliceThreads / (R_ / 4);
+        const int cth = kComposeGroups * (R_ / 4);
+        const int gc = grid_for(k_slices_compose<R_, J_>, cth, 0, kComposeGroups, g.ntiles, sms);
+        k_slices_compose<R_, J_><<<gc, cth, 0, st>>>(g);
+        const int gb = grid_for(k_slices_combine<R_, J_>, kSliceThreads, 0, gpb, g.ntiles, sms);
+        k_slices_combine<R_, J_><<<gb, kSliceThreads, 0, st>>>(g);
+    });
     return cudaGetLastError();
 }
 

@@ -130,7 +130,122 @@ struct SliceArgs {
     int64_t Lseq;            // crossing slices longer than this are split into maps
     int64_t ntiles;
     float *maps;             // [ntiles][2][J*J + J]
+    // fiber-shared v (set for the fiber variant of the factor pass)
+    const int32_t *fid;      // fiber of every slice position (-1: bad data)
+    const float *V;          // [nfibers][J]: v = B^(n) p of every fiber
+    int64_t nfibers;
 };
+
+// The lane's J/T entries of v = B^(n) p from the lane's 4 entries of p: a
+// partial matrix-vector product over the lane's r, then a reduce-scatter over
+// the group (lane `sub` ends with entries [sub*J/T, (sub+1)*J/T)).
+template <int R, int J>
+__device__ __forceinline__ void v_from_p(const float *sB, const float4 &p, int sub, unsigned m,
+                                         float (&vq)[J / (R / 4)]) {
+    constexpr int T = R / 4;
+    float vp[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+        vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
+    }
+    group_reduce_scatter_m<T, J>(vp, sub, m);
+#pragma unroll
+    for (int q = 0; q < J / T; ++q) vq[q] = vp[q];
+}
+
+// Walk over slice positions [s0, s1) that reads v from the per-fiber table
+// instead of gathering the other modes' rows: the ring holds the fiber ids of
+// positions t+D..t+2D-1 and the lane's v entries of positions t..t+D-1.
+template <int R, int J, int DMAX, bool WITH_ROW, typename Body>
+__device__ __forceinline__ void walk_v(const SliceArgs &g, int64_t s0, int64_t s1, int sub,
+                                       Body &&body) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int D = DMAX < 4 ? DMAX : 4;
+    const PassArgs &a = g.a;
+    struct Raw {
+        int32_t f, row;
+        float x;
+        bool valid;
+    };
+    auto load_raw = [&](int64_t t, bool valid, Raw &c) {
+        c.valid = valid;
+        c.f = valid ? __ldg(g.fid + t) : -1;
+        c.row = (WITH_ROW && valid) ? __ldg(a.idx[a.n] + t) : -1;
+        c.x = valid ? __ldg(a.val + t) : 0.f;
+    };
+    auto load_v = [&](const Raw &c, float (&v)[JL], bool &ok, int32_t &row) {
+        bool bad = (uint64_t)(int64_t)c.f >= (uint64_t)g.nfibers;
+        row = c.row;
+        if (WITH_ROW && (uint32_t)row >= (uint32_t)a.dims[a.n]) {
+            bad = true;
+            row = -1;
+        }
+        if (c.valid && bad) atomicOr(a.err, kErrIndex);
+        ok = c.valid && !bad;
+        const float *src = g.V + (int64_t)(ok ? c.f : 0) * J + sub * JL;
+        if constexpr (JL >= 4) {
+#pragma unroll
+            for (int q = 0; q < JL / 4; ++q) {
+                const float4 u = ok ? ldg4(src + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+            }
+        } else if constexpr (JL == 2) {
+            const float2 u = ok ? __ldg(reinterpret_cast<const float2 *>(src)) : make_float2(0.f, 0.f);
+            v[0] = u.x; v[1] = u.y;
+        } else {
+            v[0] = ok ? __ldg(src) : 0.f;
+        }
+    };
+    float ring[D][JL];
+    float rx[D];
+    bool rok[D];
+    int32_t rrow[D];
+    Raw cring[D];
+    {
+        Raw tmp[D];
+#pragma unroll
+        for (int u = 0; u < D; ++u) load_raw(s0 + u, s0 + u < s1, tmp[u]);
+#pragma unroll
+        for (int u = 0; u < D; ++u) load_raw(s0 + D + u, s0 + D + u < s1, cring[u]);
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            load_v(tmp[u], ring[u], rok[u], rrow[u]);
+            rx[u] = tmp[u].x;
+        }
+    }
+    for (int64_t t = s0; t < s1; t += D) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            if (t + u < s1) {
+                body(rrow[u], rx[u], rok[u], ring[u]);
+                load_v(cring[u], ring[u], rok[u], rrow[u]);
+                rx[u] = cring[u].x;
+                load_raw(t + u + 2 * D, t + u + 2 * D < s1, cring[u]);
+            }
+        }
+    }
+}
+
+// Calls step(row, x, ok, vq) for positions [s0, s1) in order, where vq is the
+// lane's J/T entries of v: computed from the gathered rows (FV = false) or
+// read from the per-fiber table (FV = true).
+template <bool FV, int NB, int R, int J, typename CT, int DMAX, bool WITH_ROW, typename Step>
+__device__ __forceinline__ void walk_steps(const SliceArgs &g, const float *sB, int64_t s0,
+                                           int64_t s1, int sub, unsigned m, Step &&step) {
+    constexpr int JL = J / (R / 4);
+    if constexpr (FV) {
+        walk_v<R, J, DMAX, WITH_ROW>(g, s0, s1, sub, step);
+    } else {
+        walk<NB, R, CT, DMAX, WITH_ROW>(g.a, s0, s1, sub,
+                                        [&](int32_t row, float x, bool ok, const float4 &p) {
+                                            float vq[JL];
+                                            v_from_p<R, J>(sB, p, sub, m, vq);
+                                            step(row, x, ok, vq);
+                                        });
+    }
+}
 
 // Slice [s, e) of row r is consistent with the layout and the position bounds.
 __device__ __forceinline__ bool slice_ok(const SliceArgs &g, int64_t s, int64_t e) {
@@ -155,7 +270,7 @@ __device__ __forceinline__ void store_run(float *p, const float (&r)[L]) {
 // Runs positions [s0, s1) of slice r element by element.  The lane holds the
 // JL entries [sub*JL, (sub+1)*JL) of a_r.  The next position's coordinates and
 // cached rows are loaded while the current one is computed.
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, int32_t r,
                                            int64_t s0, int64_t s1, int sub, unsigned m) {
     constexpr int T = R / 4;
@@ -180,17 +295,11 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
             for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
         }
     };
-    walk<NB, R, CT, 4, false>(a, s0, s1, sub, [&](int32_t, float x, bool ok, const float4 &p) {
-        float vp[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
-            vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
-        }
-        group_reduce_scatter_m<T, J>(vp, sub, m);
+    walk_steps<FV, NB, R, J, CT, 4, false>(g, sB, s0, s1, sub, m,
+                                           [&](int32_t, float x, bool ok, const float (&v)[JL]) {
         if (have) apply();
 #pragma unroll
-        for (int q = 0; q < JL; ++q) vq[q] = vp[q];
+        for (int q = 0; q < JL; ++q) vq[q] = v[q];
         xq = x;
         okq = ok;
         have = true;
@@ -223,7 +332,7 @@ constexpr int kSliceThreads = 256;
 // tile's first run if its slice started before the tile and its last run if
 // its slice continues after it; the factor row is switched in place whenever
 // the slice changes.
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles(SliceArgs g) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
@@ -264,26 +373,21 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
         float av[JL];
 #pragma unroll
         for (int q = 0; q < JL; ++q) av[q] = 0.f;
-        walk<NB, R, CT, 4, true>(a, q0, q1, sub, [&](int32_t row, float x, bool ok, const float4 &p) {
+        walk_steps<FV, NB, R, J, CT, 4, true>(g, sB, q0, q1, sub, m,
+                                              [&](int32_t row, float x, bool ok,
+                                                  const float (&vq)[JL]) {
             if (row != cur) {  // the slice changes: write the finished row, read the next
                 if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
                 cur = row;
                 if (cur >= 0) load_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
             }
-            float vp[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
-                vp[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
-            }
-            group_reduce_scatter_m<T, J>(vp, sub, m);
             float dot = 0.f;
 #pragma unroll
-            for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vp[q], dot);
+            for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vq[q], dot);
             const float e = x - group_sum_m<T>(dot, m);
             if (ok) {
 #pragma unroll
-                for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vp[q] - a.lam * av[q]);
+                for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
             }
         });
         if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
@@ -292,7 +396,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
 
 // Crossing slices of at most Lseq nonzeros, whole, one per lane group (the
 // group that owns the slice's first tile boundary).
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chains(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
@@ -307,7 +411,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
         int32_t r;
         int64_t s, e;
         if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
-            run_direct<NB, R, J, CT>(g, sB, r, s, e, sub, m);
+            run_direct<FV, NB, R, J, CT>(g, sB, r, s, e, sub, m);
     }
 }
 
@@ -315,7 +419,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
 // Composes the steps of positions [s0, s1) of one slice into the affine map
 // (M, c) with a_after = M a_before + c.  The lane holds rows [sub*JL, ...) of M
 // and c.
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, int64_t s0,
                                             int64_t s1, int sub, unsigned m, float *out) {
     constexpr int T = R / 4;
@@ -385,14 +489,8 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         }
     };
     // prefetch depth 1: with the pipelined step a deeper ring spills (measured)
-    walk<NB, R, CT, 1, false>(a, s0, s1, sub, [&](int32_t, float x0, bool ok0, const float4 &p) {
-        float v[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
-            v[j] = fmaf(b.x, p.x, fmaf(b.y, p.y, fmaf(b.z, p.z, b.w * p.w)));
-        }
-        group_reduce_scatter_m<T, J>(v, sub, m);  // v[0..JL): the lane's slice of v
+    walk_steps<FV, NB, R, J, CT, 1, false>(g, sB, s0, s1, sub, m,
+                                           [&](int32_t, float x0, bool ok0, const float (&v)[JL]) {
         if (have) apply();
 #pragma unroll
         for (int q = 0; q < JL; ++q) vq[q] = v[q];
@@ -410,7 +508,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 // One group per tile: maps for the tile's first run (if its slice started
 // before the tile) and last run (if its slice continues after the tile) when
 // that slice is longer than Lseq.
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
@@ -439,10 +537,10 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
             // slot 0: run that started before the tile; slot 1: run that starts in
             // the tile and continues after it
             if (side == 0 && before) {
-                compose_map<NB, R, J, CT>(g, sB, p0, min(e, p1), sub, m,
+                compose_map<FV, NB, R, J, CT>(g, sB, p0, min(e, p1), sub, m,
                                       g.maps + (t * 2 + 0) * (int64_t)(J * J + J));
             } else if (side == 1 && after && !before) {
-                compose_map<NB, R, J, CT>(g, sB, max(s, p0), p1, sub, m,
+                compose_map<FV, NB, R, J, CT>(g, sB, max(s, p0), p1, sub, m,
                                       g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
             }
         }
@@ -547,21 +645,23 @@ inline int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block,
 // The three kernels touch disjoint data (chains and tiles write different
 // factor rows, maps write only the map workspace), so they may run on three
 // streams at once.
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
     if (g.ntiles > 1) {
-        const int gch = grid_for(k_slices_chains<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles - 1, sms);
-        k_slices_chains<NB, R, J, CT><<<gch, kSliceThreads, 0, ss.chains>>>(g);
+        const int gch = grid_for(k_slices_chains<FV, NB, R, J, CT>, kSliceThreads, 0, gpb,
+                                 g.ntiles - 1, sms);
+        k_slices_chains<FV, NB, R, J, CT><<<gch, kSliceThreads, 0, ss.chains>>>(g);
         *launches += 1;
     }
-    const int gd = grid_for(k_slices_tiles<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
-    k_slices_tiles<NB, R, J, CT><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
+    const int gd = grid_for(k_slices_tiles<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
+    k_slices_tiles<FV, NB, R, J, CT><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
     *launches += 1;
     if (with_maps && g.ntiles > 1) {
-        const int gm = grid_for(k_slices_maps<NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
-        k_slices_maps<NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
+        const int gm = grid_for(k_slices_maps<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles,
+                                sms);
+        k_slices_maps<FV, NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
         *launches += 1;
     }
 }
@@ -598,5 +698,9 @@ SFT_SLICE_WRAPPERS(3, bf16)
 SFT_SLICE_WRAPPERS(7, bf16)
 SFT_SLICE_WRAPPERS(15, bf16)
 #undef SFT_SLICE_WRAPPERS
+cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms);
+// fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
+void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,
+                      int sms, int64_t *launches);
 
 }  // namespace sft

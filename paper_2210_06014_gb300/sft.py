@@ -35,7 +35,8 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_epoch", "sft_batch_loss", "sft_batch_snapshot_bytes", "sft_batch_autotune",
             "sft_batch_sync", "sft_batch_launch_count", "sft_batch_epoch_tasks",
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
-            "sft_batch_set_wait_limit", "sft_batch_hold_pass"]
+            "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
+            "sft_group_fibers", "sft_update_factors_fibers"]
 
 
 class SftError(RuntimeError):
@@ -162,6 +163,14 @@ def load(build_if_missing: bool = True):
     lib.sft_batch_plan.restype = i64
     lib.sft_batch_destroy.argtypes = [vp]
     lib.sft_batch_destroy.restype = None
+    lib.sft_fibers_scratch_bytes.argtypes = [i64]
+    lib.sft_fibers_scratch_bytes.restype = ctypes.c_size_t
+    lib.sft_group_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), i64, vp, vp,
+                                     ctypes.POINTER(i64), vp, ctypes.c_size_t]
+    lib.sft_group_fibers.restype = ctypes.c_int
+    lib.sft_update_factors_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, vp, vp,
+                                              i64, vp, f32, f32, vp, ctypes.c_size_t]
+    lib.sft_update_factors_fibers.restype = ctypes.c_int
     lib.sft_loss_grad_C.argtypes = [ctx, ctypes.POINTER(vp), vp, i64, ctypes.POINTER(vp), i32, vp]
     lib.sft_loss_grad_C.restype = ctypes.c_int
     lib.sft_grad_AB.argtypes = [ctx, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -361,6 +370,31 @@ def sft_grad_AB(ctx, dC, scale: Optional[torch.Tensor], gA, gB) -> None:
                                      _ptr_array(gB)), "sft_grad_AB")
 
 
+def sft_fibers_scratch_bytes(nnz: int) -> int:
+    return int(load().sft_fibers_scratch_bytes(int(nnz)))
+
+
+def sft_group_fibers(ctx, mode, sidx, nnz, fid, frep, scratch: torch.Tensor) -> int:
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib, ctx, lib.sft_group_fibers(ctx, int(mode), _ptr_array(sidx), int(nnz), _ptr(fid),
+                                          _ptr(frep), ctypes.byref(n), _ptr(scratch),
+                                          scratch.numel() * scratch.element_size()),
+           "sft_group_fibers")
+    return int(n.value)
+
+
+def sft_update_factors_fibers(ctx, mode, sidx, sval, row_ptr, nnz, fid, frep, nfibers, V, lr, lam,
+                              workspace: torch.Tensor) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_update_factors_fibers(ctx, int(mode), _ptr_array(sidx), _ptr(sval),
+                                                   _ptr(row_ptr), int(nnz), _ptr(fid), _ptr(frep),
+                                                   int(nfibers), _ptr(V), float(lr), float(lam),
+                                                   _ptr(workspace),
+                                                   workspace.numel() * workspace.element_size()),
+           "sft_update_factors_fibers")
+
+
 class Slices:
     """The slice layout of one mode (device tensors): idx (N int32 arrays),
     val (float32) and row_ptr (I_n + 1 int32), built by sft_group_slices."""
@@ -378,6 +412,27 @@ class Slices:
         sft_group_slices(dec.ctx, mode, idx, val, perm, nnz, self.idx, self.val, self.row_ptr,
                          scratch)
         self._scratch = scratch  # kept alive until the enqueued work has run
+        self.fid = self.frep = self.V = None
+        self.nfibers = 0
+        self._J = dec.J[mode]
+
+    def build_fibers(self, dec: "Decomposition") -> int:
+        """Fiber ids of the layout (sft_group_fibers) and a v buffer; the factor
+        pass then forms v once per fiber.  Returns the number of fibers."""
+        dev = self.val.device
+        self.fid = torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
+        self.frep = torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
+        scratch = torch.empty(max(16, sft_fibers_scratch_bytes(self.nnz)), dtype=torch.uint8,
+                              device=dev)
+        self.nfibers = sft_group_fibers(dec.ctx, self.mode, self.idx, self.nnz, self.fid,
+                                        self.frep, scratch)
+        del scratch
+        self.V = torch.empty(max(1, self.nfibers), self._J, dtype=torch.float32, device=dev)
+        return self.nfibers
+
+    def drop_fibers(self):
+        self.fid = self.frep = self.V = None
+        self.nfibers = 0
 
 
 # ----------------------------------------------------------------------------- owner object
@@ -456,8 +511,12 @@ class Decomposition:
         if ws is None or ws.numel() < need:
             ws = torch.empty(need, dtype=torch.uint8, device=sl.val.device)
             self._slice_ws = ws
-        sft_update_factors_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, lr, lam,
-                                  ws)
+        if sl.fid is not None:
+            sft_update_factors_fibers(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, sl.fid,
+                                      sl.frep, sl.nfibers, sl.V, lr, lam, ws)
+        else:
+            sft_update_factors_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, lr,
+                                      lam, ws)
 
     def update_core_slices(self, sl: Slices, batch=None, lr=0.01, lam=0.01):
         sft_update_core_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz,

@@ -384,3 +384,91 @@ def test_bf16_epochs_rmse(sft, oracle_mod, skewed):
         ref.epoch(ix, xv, None, None, batch_factor=1, batch_core=T.nnz)
         got, want = dec.rmse(idx, val), ref.rmse(ix, xv)
         assert abs(got / want - 1) < 0.01, (ep, got, want)
+
+
+# ----------------------------------------------------------------------------- fiber-shared v
+
+
+@functools.lru_cache(maxsize=None)
+def dense_small(order=3, dims=(30, 20, 10), nnz=3000, J=8, seed=5):
+    """A small, dense-ish tensor: every fiber of every mode holds several nonzeros."""
+    from paper_2210_06014_gb300 import synth
+    spec = synth.TensorSpec(f"dense{order}", dims, nnz, (J,) * order, J, ("uniform",) * order,
+                            values="planted", planted_sigma=0.4, noise_sigma=0.01, seed=seed)
+    return synth.make_tensor(spec)
+
+
+def test_fiber_layout(sft):
+    """fid groups exactly the positions that share the other modes' coordinates,
+    frep points at a member of each fiber, and the count is the number of
+    distinct tuples."""
+    T = dense_small()
+    idx, val = to_dev(T)
+    dec = sft.Decomposition(T.A0, T.B0)
+    for n in range(3):
+        sl = dec.slices(n, idx, val, None)
+        nf = sl.build_fibers(dec)
+        sidx = [i.cpu().numpy().astype(np.int64) for i in sl.idx]
+        others = [k for k in range(3) if k != n]
+        tup = np.stack([sidx[k] for k in others], axis=1)
+        uniq, inv = np.unique(tup, axis=0, return_inverse=True)
+        assert nf == len(uniq)
+        fid = sl.fid.cpu().numpy()[:T.nnz]
+        assert fid.min() >= 0 and fid.max() < nf
+        # same tuple <-> same fiber id
+        pairs = set(zip(inv.ravel().tolist(), fid.tolist()))
+        assert len(pairs) == nf
+        frep = sl.frep.cpu().numpy()[:nf]
+        assert all(fid[frep[f]] == f for f in range(nf))
+
+
+@pytest.mark.parametrize("case", ["dense_tiled", "dense_maps", "dense_chains", "small", "order5",
+                                  "bf16"])
+def test_fiber_pass_equals_row_pass(sft, case):
+    """The factor pass with v formed once per fiber gives the same bits as the
+    per-nonzero path (same operations in the same order), for every mode."""
+    prec = sft.SFT_BF16 if case == "bf16" else sft.SFT_FP32
+    tiling = {"dense_tiled": (0, 0), "dense_maps": (32, -1), "dense_chains": (32, 1 << 30),
+              "small": (0, 0), "order5": (32, -1), "bf16": (32, -1)}[case]
+    if case == "small":
+        T = small_tensor()
+    elif case == "order5":
+        T = high_order_tensor("order5_J16")
+    else:
+        T = dense_small()
+    idx, val = to_dev(T)
+    N = len(idx)
+    outs = []
+    for use_fibers in (False, True):
+        dec = sft.Decomposition(T.A0, T.B0, prec=prec)
+        dec.set_slice_tiling(*tiling)
+        for n in range(N):
+            sl = dec.slices(n, idx, val, None)
+            if use_fibers:
+                sl.build_fibers(dec)
+            dec.update_factors_slices(sl, lr=0.002, lam=0.01)
+            dec.refresh(n)
+        dec.sync(60_000)
+        outs.append([a.clone() for a in dec.A])
+    for n, (a, b) in enumerate(zip(*outs)):
+        assert torch.equal(a, b), (case, n, (a - b).abs().max().item())
+
+
+def test_fiber_pass_on_skewed_tensor_matches_oracle(sft, oracle_mod, skewed):
+    """Zipf slices (maps) with fibers: equal to the element-by-element oracle pass."""
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        A0 = dec.A[n].cpu().numpy().astype(np.float64)
+        sl = dec.slices(n, idx, val, None)
+        nf = sl.build_fibers(dec)
+        assert 0 < nf <= T.nnz
+        dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+        dec.sync(60_000)
+        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
+        assert rel_fro(got, ref.A[n]) < TOL32, n
