@@ -716,7 +716,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             torch.cuda.synchronize()
             layout_s += time.perf_counter() - t0
     fibers = [{"mode": n, "fibers": sl.nfibers if sl.fid is not None else None,
-               "used": sl.fid is not None} for n, sl in enumerate(slices)]
+               "used": sl.fid is not None, "core": sl.P is not None}
+              for n, sl in enumerate(slices)]
 
     ev = {}
 
@@ -806,18 +807,25 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     # factor bytes of one epoch, mode by mode: a mode with fibers reads its
     # fiber id and v (J floats) per nonzero instead of the N-1 cached rows, and
     # first forms v per fiber (N-1 coordinates and rows in, J floats out)
-    fac_epoch = 0.0
+    fac_epoch = core_epoch = 0.0
     for fb in fibers or [{"used": False}] * N:
+        gathers = 4 * (N - 1) + (N - 1) * R * c_bytes  # other coordinates + cached rows
         if fb["used"]:
             nf = fb["fibers"]
-            fac_epoch += nnz * (fac_bytes - (N - 1) * R * c_bytes - 4 * (N - 1) + 4 + J * 4)
-            fac_epoch += nf * (4 * (N - 1) + (N - 1) * R * c_bytes + J * 4 + 4)
+            # per nonzero: fiber id and v (J) / p (R) instead of the cached rows;
+            # per fiber: its coordinates and rows in, v or p out
+            fac_epoch += nnz * (fac_bytes - gathers + 4 + J * 4) + nf * (4 + gathers + J * 4)
+            if fb["core"]:
+                core_epoch += nnz * (core_bytes - gathers + 4 + R * 4) + nf * (4 + gathers + R * 4)
+            else:
+                core_epoch += nnz * core_bytes
         else:
             fac_epoch += nnz * fac_bytes
+            core_epoch += nnz * core_bytes
     peak, peak_kind = peaks()
     kernels = {
         "factor": (f_ms, fac_epoch / N / (f_ms / 1e3) / 1e9),
-        "core": (c_ms, core_bytes * nnz / (c_ms / 1e3) / 1e9),
+        "core": (c_ms, core_epoch / N / (c_ms / 1e3) / 1e9),
     }
     dom = "factor" if f_step >= c_step else "core"
     ach = kernels[dom][1]
@@ -829,7 +837,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     if not args.no_e2e:
         if slices:
             dev_in = [t for sl in slices for t in sl.idx + [sl.val, sl.row_ptr]]
-            dev_in += [t for sl in slices if sl.fid is not None for t in (sl.fid, sl.frep)]
+            dev_in += [t for sl in slices if sl.fid is not None
+                       for t in [sl.fid] + [c for c in sl.fcoord if c is not None]]
         else:
             dev_in = list(idx) + [val]
         dev_in += list(tidx) + [tval]
@@ -881,7 +890,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "per_step_ms": {"factor": f_step, "core": c_step, "refresh": r_step,
                                 "loss": l_step},
                 "algorithmic_bytes_per_nnz": {"factor": fac_epoch / (N * nnz),
-                                              "core": core_bytes},
+                                              "core": core_epoch / (N * nnz)},
                 "achieved_gbs": {k: v[1] for k, v in kernels.items()},
             },
             "roofline": {"bound": "hbm", "kernel": f"{dom} pass", "achieved": ach, "peak": peak,

@@ -238,32 +238,46 @@ sft_status sft_update_core_slices(sft_ctx *ctx, int32_t mode, const int32_t *con
  * ------------------------------------------------------------------------- */
 
 /* Bytes of device scratch sft_group_fibers needs (a hash table of at least
- * twice nnz slots, 16 bytes each). */
+ * twice nnz slots, 20 bytes each). */
 size_t sft_fibers_scratch_bytes(int64_t nnz);
 
 /* For the slice layout of mode n (sidx: N device pointers from
  * sft_group_slices), writes fid[pos] (DEVICE int32, nnz entries) = the fiber of
- * each position, numbered 0..nfibers-1, and frep[f] (DEVICE int32, room for
- * nnz entries) = one position of fiber f; *nfibers (HOST) receives the count.
- * The numbering depends on thread scheduling; the fibers themselves do not.
- * Synchronises the stream.  SFT_ENOTSUP if the product of the other modes'
- * lengths is 4e18 or more (the fiber key is their exact linear index).
- * Coordinates out of range get fid -1 and are reported as SFT_EINVAL. */
+ * each position, numbered 0..nfibers-1, and the fibers' coordinates:
+ * fcoord (host array of N device pointers; the entry for `mode` is ignored)
+ * with fcoord[k][f] = i_k of fiber f (DEVICE int32, room for nnz entries).
+ * *nfibers (HOST) receives the count.  The numbering depends on thread
+ * scheduling; the fibers themselves do not.  Synchronises the stream.
+ * SFT_ENOTSUP if the product of the other modes' lengths is 4e18 or more (the
+ * fiber key is their exact linear index).  Coordinates out of range get
+ * fid -1 and are reported as SFT_EINVAL. */
 sft_status sft_group_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx, int64_t nnz,
-                            int32_t *fid, int32_t *frep, int64_t *nfibers, void *scratch,
+                            int32_t *fid, int32_t *const *fcoord, int64_t *nfibers, void *scratch,
                             size_t scratch_bytes);
 
 /* sft_update_factors_slices with v formed once per fiber: first
  * V[f][0..J_n) = B^(n) p_f for every fiber (V: DEVICE float32, nfibers x J_n,
  * 16-byte aligned, caller-owned), then the element-by-element slice pass reads
- * v from V.  fid / frep / nfibers from sft_group_fibers on the same layout.
+ * v from V.  fid / fcoord / nfibers from sft_group_fibers on the same layout.
  * v is formed with the same operations in the same order as the per-nonzero
  * path, so the result is the same.  Enqueues only. */
 sft_status sft_update_factors_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
                                      const float *sval, const int32_t *row_ptr, int64_t nnz,
-                                     const int32_t *fid, const int32_t *frep, int64_t nfibers,
-                                     float *V, float lr, float lambda, void *workspace,
+                                     const int32_t *fid, const int32_t *const *fcoord,
+                                     int64_t nfibers, float *V, float lr, float lambda,
+                                     void *workspace,
                                      size_t workspace_bytes);
+
+/* sft_update_core_slices with p formed once per fiber: first
+ * P[f][0..R) = prod_{k != n} C^(k)[i_k(f)] (P: DEVICE float32, nfibers x R,
+ * 16-byte aligned, caller-owned; it does not depend on B^(n), so one fill
+ * serves every minibatch of the pass), then the core pass reads p from P.
+ * Same result as the per-nonzero path.  Enqueues only. */
+sft_status sft_update_core_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
+                                  const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                  int64_t batch, const int32_t *fid,
+                                  const int32_t *const *fcoord, int64_t nfibers, float *P,
+                                  float lr, float lambda);
 
 /* Tiling of the slice passes: tile = positions per work item (0 = automatic),
  * max_direct = longest slice that crosses a tile boundary and is still run

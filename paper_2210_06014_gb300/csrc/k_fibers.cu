@@ -43,6 +43,13 @@ struct FiberKeyArgs {
     int no;  // number of other modes
 };
 
+struct FiberCoords {
+    const int32_t *c[kMaxOrder];  // [q][f]: coordinate of other mode q of fiber f
+};
+struct FiberCoordsOut {
+    int32_t *c[kMaxOrder];
+};
+
 __global__ void k_fiber_clear(unsigned long long *table, int64_t cap) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -88,14 +95,14 @@ __global__ void k_fiber_insert(FiberKeyArgs f, int64_t nnz, unsigned long long *
 }
 
 __global__ void k_fiber_number(const unsigned long long *table, const int32_t *slot_pos,
-                               int64_t cap, int32_t *slot_fid, int32_t *frep,
+                               int64_t cap, int32_t *slot_fid, int32_t *rep,
                                unsigned long long *count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (table[i] == kEmpty) continue;
         const unsigned long long id = atomicAdd(count, 1ull);
         slot_fid[i] = (int32_t)id;
-        frep[id] = slot_pos[i];
+        rep[id] = slot_pos[i];
     }
 }
 
@@ -107,11 +114,41 @@ __global__ void k_fiber_remap(int32_t *fid, int64_t nnz, const int32_t *slot_fid
     }
 }
 
+// fcoord[q][f] = coordinate of other mode q of fiber f (read at its
+// representative position), so the per-pass kernels read them sequentially.
+__global__ void k_fiber_coords(FiberKeyArgs f, const int32_t *rep,
+                               const unsigned long long *count, FiberCoordsOut out) {
+    const int64_t nf = (int64_t)*count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t pos = rep[i];
+        for (int q = 0; q < f.no; ++q) out.c[q][i] = f.oidx[q][pos];
+    }
+}
+
+// Gathers the lane's 4 entries of every other mode's cached row of a fiber
+// whose coordinates are in ci (checked here; bad ones leave the fiber out).
+template <int R, typename CT, int NO>
+__device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci)[NO], bool ok,
+                                           int sub, Rows<NO> &w) {
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+        if (ok && q < a.N - 1 && (uint32_t)ci[q] >= (uint32_t)a.odims[q]) bad = true;
+    if (ok && bad) atomicOr(a.err, kErrIndex);
+    ok = ok && !bad;
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+        w.r[q] = (ok && q < a.N - 1) ? ldC<CT>(a.oC[q], (int64_t)ci[q] * R + 4 * sub)
+                                     : make_float4(1.f, 1.f, 1.f, 1.f);
+    return ok;
+}
+
 // V[f] = B^(n) prod_{k != n} C^(k)[i_k(f)] for every fiber; T = R/4 lanes per
-// fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  The coordinates come
-// from the fiber's representative position in the slice layout.
+// fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  The next fiber's
+// coordinates are loaded one iteration ahead.
 template <int R, int J, typename CT>
-__global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, const int32_t *frep,
+__global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords fc,
                                                          int64_t nfibers, float *V) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
@@ -125,26 +162,20 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, const int32
     // every group of a warp runs the same number of iterations (full-mask shuffles)
     const int64_t first = (int64_t)blockIdx.x * (kFibThreads / T) + threadIdx.x / T;
     const int64_t warp_first = first - (lane / T);
+    int32_t nc[NO];
+    auto fetch = [&](int64_t f) {
+#pragma unroll
+        for (int q = 0; q < NO; ++q) nc[q] = (f < nfibers && q < a.N - 1) ? __ldg(fc.c[q] + f) : 0;
+    };
+    fetch(first);
     for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
         const int64_t f = f0 + lane / T;
-        bool ok = f < nfibers;
-        int64_t pos = 0;
-        if (ok) {
-            pos = __ldg(frep + f);
-            if (pos < 0 || pos >= a.nnz) {
-                atomicOr(a.err, kErrIndex);
-                ok = false;
-            }
-        }
-        Rows<NO> w;
+        int32_t ci[NO];
 #pragma unroll
-        for (int q = 0; q < NO; ++q) {
-            w.r[q] = make_float4(1.f, 1.f, 1.f, 1.f);
-            if (ok && q < a.N - 1) {
-                const int32_t i = __ldg(a.oidx[q] + pos);
-                if ((uint32_t)i < (uint32_t)a.odims[q]) w.r[q] = ldC<CT>(a.oC[q], (int64_t)i * R + 4 * sub);
-            }
-        }
+        for (int q = 0; q < NO; ++q) ci[q] = nc[q];
+        fetch(f + stride);
+        Rows<NO> w;
+        const bool ok = fiber_rows<R, CT, NO>(a, ci, f < nfibers, sub, w);
         const float4 p = product<NO>(w);
         float vp[J];
 #pragma unroll
@@ -160,6 +191,34 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, const int32
     }
 }
 
+// P[f] = prod_{k != n} C^(k)[i_k(f)] (R floats) for every fiber: the core
+// pass's p, in the same product order as the per-nonzero walk.
+template <int R, typename CT>
+__global__ void __launch_bounds__(kFibThreads) k_fiber_p(PassArgs a, FiberCoords fc,
+                                                         int64_t nfibers, float *P) {
+    constexpr int T = R / 4;
+    constexpr int NO = kMaxOrder - 1;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const int64_t stride = (int64_t)gridDim.x * (kFibThreads / T);
+    const int64_t first = (int64_t)blockIdx.x * (kFibThreads / T) + threadIdx.x / T;
+    int32_t nc[NO];
+    auto fetch = [&](int64_t f) {
+#pragma unroll
+        for (int q = 0; q < NO; ++q) nc[q] = (f < nfibers && q < a.N - 1) ? __ldg(fc.c[q] + f) : 0;
+    };
+    fetch(first);
+    for (int64_t f = first; f < nfibers; f += stride) {
+        int32_t ci[NO];
+#pragma unroll
+        for (int q = 0; q < NO; ++q) ci[q] = nc[q];
+        fetch(f + stride);
+        Rows<NO> w;
+        if (fiber_rows<R, CT, NO>(a, ci, true, sub, w))
+            *reinterpret_cast<float4 *>(P + f * R + 4 * sub) = product<NO>(w);
+    }
+}
+
 }  // namespace
 
 int64_t fiber_table_capacity(int64_t nnz) {
@@ -168,8 +227,9 @@ int64_t fiber_table_capacity(int64_t nnz) {
     return cap;
 }
 
-cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, void *scratch,
-                                int64_t *nfibers, cudaStream_t st, int sms, int64_t *launches) {
+cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const *fcoord,
+                                void *scratch, int64_t *nfibers, cudaStream_t st, int sms,
+                                int64_t *launches) {
     const int64_t cap = fiber_table_capacity(a.nnz);
     char *p = (char *)scratch;
     unsigned long long *table = (unsigned long long *)p;
@@ -178,8 +238,11 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, 
     p += cap * sizeof(int32_t);
     int32_t *slot_fid = (int32_t *)p;
     p += cap * sizeof(int32_t);
+    int32_t *rep = (int32_t *)p;
+    p += cap * sizeof(int32_t);
     unsigned long long *count = (unsigned long long *)p;
     FiberKeyArgs f{};
+    FiberCoordsOut out{};
     f.no = a.N - 1;
     unsigned long long s = 1;
     for (int q = f.no - 1; q >= 0; --q) {
@@ -188,14 +251,17 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, 
         f.stride[q] = s;
         s *= (unsigned long long)a.odims[q];
     }
+    for (int k = 0, q = 0; k < a.N; ++k)
+        if (k != a.n) out.c[q++] = fcoord[k];
     const int blocks = sms * 8;
     k_fiber_clear<<<blocks, kFibThreads, 0, st>>>(table, cap);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_fiber_insert<<<blocks, kFibThreads, 0, st>>>(f, a.nnz, table, slot_pos, cap, fid, a.err);
-    k_fiber_number<<<blocks, kFibThreads, 0, st>>>(table, slot_pos, cap, slot_fid, frep, count);
+    k_fiber_number<<<blocks, kFibThreads, 0, st>>>(table, slot_pos, cap, slot_fid, rep, count);
     k_fiber_remap<<<blocks, kFibThreads, 0, st>>>(fid, a.nnz, slot_fid);
-    *launches += 4;
+    k_fiber_coords<<<blocks, kFibThreads, 0, st>>>(f, rep, count, out);
+    *launches += 5;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     unsigned long long h = 0;
@@ -205,8 +271,15 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, 
     return e;
 }
 
+static FiberCoords fiber_coords(const PassArgs &a, const int32_t *const *fcoord) {
+    FiberCoords fc{};
+    for (int k = 0, q = 0; k < a.N; ++k)
+        if (k != a.n) fc.c[q++] = fcoord[k];
+    return fc;
+}
+
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, const int32_t *fid, const int32_t *frep,
+                                 float *maps, const int32_t *fid, const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss_in,
                                  int sms, int64_t *launches) {
     SliceStreams ss = ss_in;
@@ -217,9 +290,9 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
         int64_t blocks = (nfibers + per_block - 1) / per_block;
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         if (a.cbf16)
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16><<<(int)blocks, kFibThreads, 0, st>>>(a, frep, nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, V)));
         else
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float><<<(int)blocks, kFibThreads, 0, st>>>(a, frep, nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, V)));
         *launches += 1;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -258,6 +331,40 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_core_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W,
+                               const int32_t *fid, const int32_t *const *fcoord, int64_t nfibers,
+                               float *P,
+                               int J, int R, float *partials, int max_blocks, cudaStream_t st,
+                               int sms, int64_t *launches, bool fill_p) {
+    if (fill_p && nfibers > 0) {
+        const int64_t per_block = kFibThreads / (R / 4);
+        int64_t blocks = (nfibers + per_block - 1) / per_block;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        if (a.cbf16)
+            SFT_DISPATCH_R(R, (k_fiber_p<R_, __nv_bfloat16><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, P)));
+        else
+            SFT_DISPATCH_R(R, (k_fiber_p<R_, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, P)));
+        *launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    SliceArgs g{};
+    g.a = a;
+    g.row_ptr = row_ptr;
+    g.W = W;
+    g.Lseq = 0;
+    g.ntiles = (a.count + W - 1) / W;
+    g.maps = nullptr;
+    g.fid = fid;
+    g.V = P;
+    g.nfibers = nfibers;
+    const int nblk = core_slices_fv(g, R, J, partials, max_blocks, st, sms);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 2;
+    return launch_core_apply(a.B, partials, nblk, J * R, a.count, a.lr, a.lam, st);
 }
 
 }  // namespace sft

@@ -7,7 +7,7 @@ int core_slices_no2_f32(const SliceArgs &g, int R, int J, float *partials, int m
                            cudaStream_t st, int sms) {
     int nblk = 1;
     dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-        nblk = core_slices_t<2, decltype(r_c)::value, decltype(j_c)::value, float>(
+        nblk = core_slices_t<false, 2, decltype(r_c)::value, decltype(j_c)::value, float>(
             g, partials, max_blocks, st, sms);
     });
     return nblk;

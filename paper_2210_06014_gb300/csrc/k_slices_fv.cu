@@ -1,5 +1,6 @@
-// k_slices_fv.cu -- factor-pass slice kernels that read v from the per-fiber
-// table (one instantiation per (R, J); they never touch the cached products).
+// k_slices_fv.cu -- slice kernels that read v (factor pass) or p (core pass)
+// from the per-fiber tables (one instantiation per (R, J); they never touch the
+// cached products).
 #include "slices_impl.cuh"
 
 namespace sft {
@@ -10,6 +11,16 @@ void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const Sl
         factor_slices_t<true, 2, decltype(r_c)::value, decltype(j_c)::value, float>(
             g, with_maps, ss, sms, launches);
     });
+}
+
+int core_slices_fv(const SliceArgs &g, int R, int J, float *partials, int max_blocks,
+                   cudaStream_t st, int sms) {
+    int nblk = 1;
+    dispatch_rj(R, J, [&](auto r_c, auto j_c) {
+        nblk = core_slices_t<true, 2, decltype(r_c)::value, decltype(j_c)::value, float>(
+            g, partials, max_blocks, st, sms);
+    });
+    return nblk;
 }
 
 }  // namespace sft

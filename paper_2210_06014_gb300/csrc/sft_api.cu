@@ -565,11 +565,11 @@ sft_status sft_update_core_slices(sft_ctx *c, int32_t mode, const int32_t *const
 
 size_t sft_fibers_scratch_bytes(int64_t nnz) {
     if (nnz < 0) return 0;
-    return (size_t)fiber_table_capacity(nnz) * 16 + 256;
+    return (size_t)fiber_table_capacity(nnz) * 20 + 256;
 }
 
 sft_status sft_group_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx, int64_t nnz,
-                            int32_t *fid, int32_t *frep, int64_t *nfibers, void *scratch,
+                            int32_t *fid, int32_t *const *fcoord, int64_t *nfibers, void *scratch,
                             size_t scratch_bytes) {
     if (!c) return SFT_EINVAL;
     if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
@@ -578,7 +578,9 @@ sft_status sft_group_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx
         if (!sidx[k] && nnz > 0) return fail(c, SFT_EINVAL, "sidx[k] is NULL");
     if (nnz < 0 || nnz > 0x7fffffffLL) return fail(c, SFT_EINVAL, "nnz must be in [0, 2^31)");
     if (!nfibers) return fail(c, SFT_EINVAL, "nfibers is NULL");
-    if ((!fid || !frep) && nnz > 0) return fail(c, SFT_EINVAL, "fid / frep are NULL");
+    if ((!fid || !fcoord) && nnz > 0) return fail(c, SFT_EINVAL, "fid / fcoord are NULL");
+    for (int k = 0; k < c->N && nnz > 0; ++k)
+        if (k != mode && !fcoord[k]) return fail(c, SFT_EINVAL, "fcoord[k] is NULL for a mode k != mode");
     if (!scratch || scratch_bytes < sft_fibers_scratch_bytes(nnz) || ((uintptr_t)scratch & 15u))
         return fail(c, SFT_EINVAL, "scratch missing, misaligned or smaller than sft_fibers_scratch_bytes");
     // the fiber key is the exact linear index of the other modes' coordinates
@@ -590,7 +592,7 @@ sft_status sft_group_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx
     *nfibers = 0;
     if (nnz == 0) return SFT_OK;
     PassArgs a = pass_args(c, mode, sidx, nullptr, nullptr, nnz, 0.f, 0.f);
-    cudaError_t e = launch_group_fibers(a, fid, frep, scratch, nfibers, c->stream, c->sms,
+    cudaError_t e = launch_group_fibers(a, fid, fcoord, scratch, nfibers, c->stream, c->sms,
                                         &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "fiber layout");
     return read_flag(c);
@@ -598,7 +600,8 @@ sft_status sft_group_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx
 
 sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
                                      const float *sval, const int32_t *row_ptr, int64_t nnz,
-                                     const int32_t *fid, const int32_t *frep, int64_t nfibers,
+                                     const int32_t *fid, const int32_t *const *fcoord,
+                                     int64_t nfibers,
                                      float *V, float lr, float lambda, void *workspace,
                                      size_t workspace_bytes) {
     if (!c) return SFT_EINVAL;
@@ -606,8 +609,10 @@ sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *co
     if (st != SFT_OK) return st;
     if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
     if (nnz == 0) return SFT_OK;
-    if (!fid || !frep || !V || nfibers < 0 || nfibers > nnz)
-        return fail(c, SFT_EINVAL, "fid / frep / V missing or nfibers outside [0, nnz]");
+    if (!fid || !fcoord || !V || nfibers < 0 || nfibers > nnz)
+        return fail(c, SFT_EINVAL, "fid / fcoord / V missing or nfibers outside [0, nnz]");
+    for (int k = 0; k < c->N; ++k)
+        if (k != mode && !fcoord[k]) return fail(c, SFT_EINVAL, "fcoord[k] is NULL for a mode k != mode");
     if (!aligned16(V)) return fail(c, SFT_EINVAL, "V must be 16-byte aligned");
     if (!workspace || workspace_bytes < sft_slices_workspace_bytes(c, mode, nnz) ||
         ((uintptr_t)workspace & 15u))
@@ -616,9 +621,36 @@ sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *co
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
     cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, W, nnz), (float *)workspace,
-                                         fid, frep, nfibers, V, c->J[mode], c->R, ss, c->sms,
+                                         fid, fcoord, nfibers, V, c->J[mode], c->R, ss, c->sms,
                                          &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "fiber factor launch");
+    return SFT_OK;
+}
+
+sft_status sft_update_core_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
+                                  const float *sval, const int32_t *row_ptr, int64_t nnz,
+                                  int64_t batch, const int32_t *fid, const int32_t *const *fcoord,
+                                  int64_t nfibers, float *P, float lr, float lambda) {
+    if (!c) return SFT_EINVAL;
+    sft_status st = check_slices(c, mode, sidx, sval, row_ptr, nnz);
+    if (st != SFT_OK) return st;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
+    if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
+    if (nnz == 0) return SFT_OK;
+    if (!fid || !fcoord || !P || nfibers < 0 || nfibers > nnz)
+        return fail(c, SFT_EINVAL, "fid / fcoord / P missing or nfibers outside [0, nnz]");
+    for (int k = 0; k < c->N; ++k)
+        if (k != mode && !fcoord[k]) return fail(c, SFT_EINVAL, "fcoord[k] is NULL for a mode k != mode");
+    if (!aligned16(P)) return fail(c, SFT_EINVAL, "P must be 16-byte aligned");
+    PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
+    for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
+        a.base = b0;
+        a.count = nnz - b0 < batch ? nnz - b0 : batch;
+        cudaError_t e = launch_core_fibers(a, row_ptr, slice_W(c, a.count), fid, fcoord, nfibers, P,
+                                           c->J[mode], c->R, c->core_partials, c->core_max_blocks,
+                                           c->stream, c->sms, &c->launches, b0 == 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fiber core launch");
+    }
     return SFT_OK;
 }
 

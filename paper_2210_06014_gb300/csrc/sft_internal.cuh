@@ -87,12 +87,18 @@ int loss_blocks_for(int64_t count, int sms);
 cudaError_t launch_predict(const PassArgs &a, int R, float *out, cudaStream_t st, int sms);
 // fibers of a slice layout and the factor pass that shares v per fiber (k_fibers.cu)
 int64_t fiber_table_capacity(int64_t nnz);
-cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *frep, void *scratch,
-                                int64_t *nfibers, cudaStream_t st, int sms, int64_t *launches);
+cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const *fcoord,
+                                void *scratch, int64_t *nfibers, cudaStream_t st, int sms,
+                                int64_t *launches);
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, const int32_t *fid, const int32_t *frep,
+                                 float *maps, const int32_t *fid, const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss,
                                  int sms, int64_t *launches);
+cudaError_t launch_core_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W,
+                               const int32_t *fid, const int32_t *const *fcoord, int64_t nfibers,
+                               float *P,
+                               int J, int R, float *partials, int max_blocks, cudaStream_t st,
+                               int sms, int64_t *launches, bool fill_p);
 // gradient of the sampled loss (k_grad.cu)
 struct GradBufs {
     float *dC[kMaxOrder];   // dL/dC^(k), I_k x R float32

@@ -488,7 +488,8 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
             if (++since == 16) fold();
         }
     };
-    // prefetch depth 1: with the pipelined step a deeper ring spills (measured)
+    // prefetch depth 1: with the pipelined step a deeper ring spills at the
+    // 128-register bound (measured on both paths)
     walk_steps<FV, NB, R, J, CT, 1, false>(g, sB, s0, s1, sub, m,
                                            [&](int32_t, float x0, bool ok0, const float (&v)[JL]) {
         if (have) apply();
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
 // Dynamic shared memory: B (J*R) then one G tile (J*R) per lane group.
 constexpr int kCoreSliceThreads = 128;
 
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_core(SliceArgs g,
                                                                    float *__restrict__ partials) {
     constexpr int T = R / 4;
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
                 *gp = v;
             }
         };
-        walk<NB, R, CT, 4, true>(a, p0, p1, sub, [&](int32_t row, float x0, bool ok0, const float4 &p) {
+        auto step = [&](int32_t row, float x0, bool ok0, const float4 &p) {
             if (row != cur) {  // a new run: close the last one, read a and w = B^T a
                 if (cur >= 0) flush();
                 cur = row;
@@ -618,7 +619,16 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
             qv.y = fmaf(ev, p.y, qv.y);
             qv.z = fmaf(ev, p.z, qv.z);
             qv.w = fmaf(ev, p.w, qv.w);
-        });
+        };
+        if constexpr (FV) {
+            // p of every position read from the per-fiber table (g.V holds P here)
+            walk_v<R, R, 4, true>(g, p0, p1, sub,
+                                  [&](int32_t row, float x0, bool ok0, const float (&pq)[4]) {
+                                      step(row, x0, ok0, make_float4(pq[0], pq[1], pq[2], pq[3]));
+                                  });
+        } else {
+            walk<NB, R, CT, 4, true>(a, p0, p1, sub, step);
+        }
         if (cur >= 0) flush();
     }
     __syncthreads();
@@ -666,17 +676,17 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
     }
 }
 
-template <int NB, int R, int J, typename CT>
+template <bool FV, int NB, int R, int J, typename CT>
 int core_slices_t(const SliceArgs &g, float *partials, int max_blocks, cudaStream_t st,
                          int sms) {
     constexpr int T = R / 4;
     const size_t smem = (size_t)(1 + kCoreSliceThreads / T) * J * R * sizeof(float);
-    cudaFuncSetAttribute(k_slices_core<NB, R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    int nblk = grid_for(k_slices_core<NB, R, J, CT>, kCoreSliceThreads, smem, kCoreSliceThreads / T,
-                        g.ntiles, sms);
+    cudaFuncSetAttribute(k_slices_core<FV, NB, R, J, CT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nblk = grid_for(k_slices_core<FV, NB, R, J, CT>, kCoreSliceThreads, smem,
+                        kCoreSliceThreads / T, g.ntiles, sms);
     if (nblk > max_blocks) nblk = max_blocks;
-    k_slices_core<NB, R, J, CT><<<nblk, kCoreSliceThreads, smem, st>>>(g, partials);
+    k_slices_core<FV, NB, R, J, CT><<<nblk, kCoreSliceThreads, smem, st>>>(g, partials);
     return nblk;
 }
 
@@ -702,5 +712,7 @@ cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t 
 // fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
 void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,
                       int sms, int64_t *launches);
+int core_slices_fv(const SliceArgs &g, int R, int J, float *partials, int max_blocks,
+                   cudaStream_t st, int sms);
 
 }  // namespace sft

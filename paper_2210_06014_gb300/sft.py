@@ -36,7 +36,7 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_sync", "sft_batch_launch_count", "sft_batch_epoch_tasks",
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
-            "sft_group_fibers", "sft_update_factors_fibers"]
+            "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers"]
 
 
 class SftError(RuntimeError):
@@ -165,12 +165,16 @@ def load(build_if_missing: bool = True):
     lib.sft_batch_destroy.restype = None
     lib.sft_fibers_scratch_bytes.argtypes = [i64]
     lib.sft_fibers_scratch_bytes.restype = ctypes.c_size_t
-    lib.sft_group_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), i64, vp, vp,
+    lib.sft_group_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), i64, vp, ctypes.POINTER(vp),
                                      ctypes.POINTER(i64), vp, ctypes.c_size_t]
     lib.sft_group_fibers.restype = ctypes.c_int
-    lib.sft_update_factors_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, vp, vp,
-                                              i64, vp, f32, f32, vp, ctypes.c_size_t]
+    lib.sft_update_factors_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, vp,
+                                              ctypes.POINTER(vp), i64, vp, f32, f32, vp,
+                                              ctypes.c_size_t]
     lib.sft_update_factors_fibers.restype = ctypes.c_int
+    lib.sft_update_core_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, i64, vp,
+                                           ctypes.POINTER(vp), i64, vp, f32, f32]
+    lib.sft_update_core_fibers.restype = ctypes.c_int
     lib.sft_loss_grad_C.argtypes = [ctx, ctypes.POINTER(vp), vp, i64, ctypes.POINTER(vp), i32, vp]
     lib.sft_loss_grad_C.restype = ctypes.c_int
     lib.sft_grad_AB.argtypes = [ctx, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -374,25 +378,36 @@ def sft_fibers_scratch_bytes(nnz: int) -> int:
     return int(load().sft_fibers_scratch_bytes(int(nnz)))
 
 
-def sft_group_fibers(ctx, mode, sidx, nnz, fid, frep, scratch: torch.Tensor) -> int:
+def sft_group_fibers(ctx, mode, sidx, nnz, fid, fcoord, scratch: torch.Tensor) -> int:
+    """fcoord: list of N int32 device tensors (None for `mode`)."""
     lib = load()
     n = ctypes.c_int64()
     _check(lib, ctx, lib.sft_group_fibers(ctx, int(mode), _ptr_array(sidx), int(nnz), _ptr(fid),
-                                          _ptr(frep), ctypes.byref(n), _ptr(scratch),
+                                          _ptr_array(fcoord), ctypes.byref(n), _ptr(scratch),
                                           scratch.numel() * scratch.element_size()),
            "sft_group_fibers")
     return int(n.value)
 
 
-def sft_update_factors_fibers(ctx, mode, sidx, sval, row_ptr, nnz, fid, frep, nfibers, V, lr, lam,
+def sft_update_factors_fibers(ctx, mode, sidx, sval, row_ptr, nnz, fid, fcoord, nfibers, V, lr, lam,
                               workspace: torch.Tensor) -> None:
     lib = load()
     _check(lib, ctx, lib.sft_update_factors_fibers(ctx, int(mode), _ptr_array(sidx), _ptr(sval),
-                                                   _ptr(row_ptr), int(nnz), _ptr(fid), _ptr(frep),
+                                                   _ptr(row_ptr), int(nnz), _ptr(fid),
+                                                   _ptr_array(fcoord),
                                                    int(nfibers), _ptr(V), float(lr), float(lam),
                                                    _ptr(workspace),
                                                    workspace.numel() * workspace.element_size()),
            "sft_update_factors_fibers")
+
+
+def sft_update_core_fibers(ctx, mode, sidx, sval, row_ptr, nnz, batch, fid, fcoord, nfibers, P, lr,
+                           lam) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_update_core_fibers(ctx, int(mode), _ptr_array(sidx), _ptr(sval),
+                                                _ptr(row_ptr), int(nnz), int(batch), _ptr(fid),
+                                                _ptr_array(fcoord), int(nfibers), _ptr(P), float(lr),
+                                                float(lam)), "sft_update_core_fibers")
 
 
 class Slices:
@@ -412,26 +427,39 @@ class Slices:
         sft_group_slices(dec.ctx, mode, idx, val, perm, nnz, self.idx, self.val, self.row_ptr,
                          scratch)
         self._scratch = scratch  # kept alive until the enqueued work has run
-        self.fid = self.frep = self.V = None
+        self.fid = self.fcoord = self.V = self.P = None
         self.nfibers = 0
         self._J = dec.J[mode]
+        self._R = dec.R
 
-    def build_fibers(self, dec: "Decomposition") -> int:
+    # A per-fiber p table pays in the core pass only while it stays in L2: the
+    # per-nonzero path gathers cached rows that are L2-resident anyway.
+    CORE_FIBER_BYTES = 96 << 20
+
+    def build_fibers(self, dec: "Decomposition", core=None) -> int:
         """Fiber ids of the layout (sft_group_fibers) and a v buffer; the factor
-        pass then forms v once per fiber.  Returns the number of fibers."""
+        pass then forms v once per fiber.  core=None: also a p buffer for the
+        core pass when it is at most CORE_FIBER_BYTES; True / False force it.
+        Returns the number of fibers."""
         dev = self.val.device
         self.fid = torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
-        self.frep = torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
+        self.fcoord = [None if k == self.mode else
+                       torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
+                       for k in range(len(self.idx))]
         scratch = torch.empty(max(16, sft_fibers_scratch_bytes(self.nnz)), dtype=torch.uint8,
                               device=dev)
         self.nfibers = sft_group_fibers(dec.ctx, self.mode, self.idx, self.nnz, self.fid,
-                                        self.frep, scratch)
+                                        self.fcoord, scratch)
         del scratch
         self.V = torch.empty(max(1, self.nfibers), self._J, dtype=torch.float32, device=dev)
+        if core is None:
+            core = self.nfibers * self._R * 4 <= self.CORE_FIBER_BYTES
+        self.P = (torch.empty(max(1, self.nfibers), self._R, dtype=torch.float32, device=dev)
+                  if core else None)
         return self.nfibers
 
     def drop_fibers(self):
-        self.fid = self.frep = self.V = None
+        self.fid = self.fcoord = self.V = self.P = None
         self.nfibers = 0
 
 
@@ -513,14 +541,18 @@ class Decomposition:
             self._slice_ws = ws
         if sl.fid is not None:
             sft_update_factors_fibers(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, sl.fid,
-                                      sl.frep, sl.nfibers, sl.V, lr, lam, ws)
+                                      sl.fcoord, sl.nfibers, sl.V, lr, lam, ws)
         else:
             sft_update_factors_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, lr,
                                       lam, ws)
 
     def update_core_slices(self, sl: Slices, batch=None, lr=0.01, lam=0.01):
-        sft_update_core_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz,
-                               batch or sl.nnz, lr, lam)
+        if sl.fid is not None and sl.P is not None:
+            sft_update_core_fibers(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz,
+                                   batch or sl.nnz, sl.fid, sl.fcoord, sl.nfibers, sl.P, lr, lam)
+        else:
+            sft_update_core_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz,
+                                   batch or sl.nnz, lr, lam)
 
     def loss(self, idx, val):
         return sft_loss(self.ctx, idx, val, val.numel())

@@ -400,8 +400,8 @@ def dense_small(order=3, dims=(30, 20, 10), nnz=3000, J=8, seed=5):
 
 def test_fiber_layout(sft):
     """fid groups exactly the positions that share the other modes' coordinates,
-    frep points at a member of each fiber, and the count is the number of
-    distinct tuples."""
+    fcoord holds each fiber's tuple, and the count is the number of distinct
+    tuples."""
     T = dense_small()
     idx, val = to_dev(T)
     dec = sft.Decomposition(T.A0, T.B0)
@@ -418,8 +418,8 @@ def test_fiber_layout(sft):
         # same tuple <-> same fiber id
         pairs = set(zip(inv.ravel().tolist(), fid.tolist()))
         assert len(pairs) == nf
-        frep = sl.frep.cpu().numpy()[:nf]
-        assert all(fid[frep[f]] == f for f in range(nf))
+        fc = np.stack([sl.fcoord[k].cpu().numpy()[:nf] for k in others], axis=1)
+        assert np.array_equal(fc[fid], tup)
 
 
 @pytest.mark.parametrize("case", ["dense_tiled", "dense_maps", "dense_chains", "small", "order5",
@@ -472,3 +472,28 @@ def test_fiber_pass_on_skewed_tensor_matches_oracle(sft, oracle_mod, skewed):
         got = dec.A[n].cpu().numpy().astype(np.float64)
         assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n
+
+
+@pytest.mark.parametrize("case", ["dense", "small_batches", "order5", "bf16"])
+def test_fiber_core_pass_equals_row_pass(sft, case):
+    """The core pass with p read from the per-fiber table gives the same bits as
+    the per-nonzero path, whole-pass and in minibatches."""
+    prec = sft.SFT_BF16 if case == "bf16" else sft.SFT_FP32
+    T = {"dense": dense_small(), "small_batches": small_tensor(),
+         "order5": high_order_tensor("order5_J16"), "bf16": dense_small()}[case]
+    batch = 4096 if case == "small_batches" else None
+    idx, val = to_dev(T)
+    N = len(idx)
+    outs = []
+    for use_fibers in (False, True):
+        dec = sft.Decomposition(T.A0, T.B0, prec=prec)
+        for n in range(N):
+            sl = dec.slices(n, idx, val, None)
+            if use_fibers:
+                sl.build_fibers(dec, core=True)
+            dec.update_core_slices(sl, batch=batch, lr=0.5, lam=0.01)
+            dec.refresh(n)
+        dec.sync(60_000)
+        outs.append([b.clone() for b in dec.B])
+    for n, (a, b) in enumerate(zip(*outs)):
+        assert torch.equal(a, b), (case, n, (a - b).abs().max().item())
