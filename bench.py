@@ -715,6 +715,13 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                     sl.drop_fibers()
             torch.cuda.synchronize()
             layout_s += time.perf_counter() - t0
+    chain_limits = []
+    if slices and args.slice_max_direct == 0 and args.slice_tile == 0:
+        # per-mode choice of the longest slice run whole (setup, untimed; A restored)
+        t0 = time.perf_counter()
+        chain_limits = [dec.autotune_slices(sl, lr=lr, lam=0.01) for sl in slices]
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
     fibers = [{"mode": n, "fibers": sl.nfibers if sl.fid is not None else None,
                "used": sl.fid is not None, "core": sl.P is not None}
               for n, sl in enumerate(slices)]
@@ -884,6 +891,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "layout_build_s": round(layout_s, 3),
                 "factor_rows_per_nnz": rows_per_nnz,
                 "fibers": fibers,
+                "chain_limit_per_mode": chain_limits,
                 "l2": "inputs larger than L2 (COO 1.6 GB)", "generation_s": round(gen_s, 2),
                 "test_rmse_after": test_rmse,
                 "per_launch_ms": {"factor": f_ms, "core": c_ms, "refresh": r_ms, "loss": l_ms},

@@ -215,9 +215,10 @@ size_t sft_slices_workspace_bytes(const sft_ctx *ctx, int32_t mode, int64_t nnz)
  * their stored order, so the result equals the sequential pass over the visit
  * order that built the layout (slices of one mode never interact during a
  * factor pass).  Long slices are cut into tile-sized pieces composed as affine
- * maps and applied in order (same recurrence, re-associated).  Deterministic,
- * no atomics.  workspace: device buffer of sft_slices_workspace_bytes bytes.
- * Enqueues only. */
+ * maps and applied in order (same recurrence, re-associated).  Deterministic:
+ * the only atomic collects the list of slices run whole, whose order affects
+ * no result.  workspace: device buffer of sft_slices_workspace_bytes bytes
+ * (the piece maps and that list).  Enqueues only. */
 sft_status sft_update_factors_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
                                      const float *sval, const int32_t *row_ptr, int64_t nnz,
                                      float lr, float lambda, void *workspace,
@@ -285,6 +286,24 @@ sft_status sft_update_core_fibers(sft_ctx *ctx, int32_t mode, const int32_t *con
  * crossing slice is split into maps).  Results do not depend on it beyond
  * rounding. */
 sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
+
+/* Per-mode autotuner of the slice factor pass: times the pass of `mode` with
+ * several limits on the length of a crossing slice that is run whole as one
+ * chain (2W, 1024 .. 16384, and every crossing slice; longer ones go through
+ * maps) and keeps the fastest for this mode.  It overrides the tiling's
+ * max_direct for that mode until sft_set_slice_tiling is called again.  Every
+ * trial starts from the same A^(mode): it is saved to scratch (DEVICE,
+ * >= I_mode * J_mode floats, 16-byte aligned) first and restored after each
+ * trial, so the model is left as it was.  fid / fcoord / nfibers / V as for
+ * sft_update_factors_fibers, or fid = NULL for the per-nonzero path.  The
+ * choice does not change any result beyond rounding order.  Synchronous;
+ * *lseq_out (HOST, may be NULL) receives the chosen limit. */
+sft_status sft_autotune_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
+                               const float *sval, const int32_t *row_ptr, int64_t nnz,
+                               const int32_t *fid, const int32_t *const *fcoord, int64_t nfibers,
+                               float *V, float lr, float lambda, void *workspace,
+                               size_t workspace_bytes, void *scratch, size_t scratch_bytes,
+                               int64_t *lseq_out);
 
 /* ---------------------------------------------------------------------------
  * Factor pass without any device allocation.  The paper has no counterpart to

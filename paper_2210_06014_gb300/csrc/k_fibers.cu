@@ -130,7 +130,7 @@ __global__ void k_fiber_coords(FiberKeyArgs f, const int32_t *rep,
 // whose coordinates are in ci (checked here; bad ones leave the fiber out).
 template <int R, typename CT, int NO>
 __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci)[NO], bool ok,
-                                           int sub, Rows<NO> &w) {
+                                           int sub, Rows<NO, CT> &w) {
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
@@ -139,8 +139,8 @@ __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci
     ok = ok && !bad;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (ok && q < a.N - 1) ? ldC<CT>(a.oC[q], (int64_t)ci[q] * R + 4 * sub)
-                                     : make_float4(1.f, 1.f, 1.f, 1.f);
+        w.r[q] = (ok && q < a.N - 1) ? ldC_raw<CT>(a.oC[q], (int64_t)ci[q] * R + 4 * sub)
+                                     : c_one<CT>();
     return ok;
 }
 
@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords
 #pragma unroll
         for (int q = 0; q < NO; ++q) ci[q] = nc[q];
         fetch(f + stride);
-        Rows<NO> w;
+        Rows<NO, CT> w;
         const bool ok = fiber_rows<R, CT, NO>(a, ci, f < nfibers, sub, w);
-        const float4 p = product<NO>(w);
+        const float4 p = product<NO, CT>(w);
         float vp[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_p(PassArgs a, FiberCoords
 #pragma unroll
         for (int q = 0; q < NO; ++q) ci[q] = nc[q];
         fetch(f + stride);
-        Rows<NO> w;
+        Rows<NO, CT> w;
         if (fiber_rows<R, CT, NO>(a, ci, true, sub, w))
-            *reinterpret_cast<float4 *>(P + f * R + 4 * sub) = product<NO>(w);
+            *reinterpret_cast<float4 *>(P + f * R + 4 * sub) = product<NO, CT>(w);
     }
 }
 
@@ -318,6 +318,11 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.V = V;
     g.nfibers = nfibers;
     const bool with_maps = maps != nullptr;
+    {
+        cudaError_t e = launch_chain_list(g, (char *)maps + slice_maps_bytes(g.ntiles, J), ss.chains,
+                                          sms, launches);
+        if (e != cudaSuccess) return e;
+    }
     factor_slices_fv(g, R, J, with_maps, ss, sms, launches);
     if (fork) {
         cudaEventRecord(ss.chains_done, ss.chains);

@@ -357,6 +357,40 @@ int slice_tile_length(int64_t nnz, int sms) {
     return (int)W;
 }
 
+// The pass's chain list: every crossing slice (one that spans a tile
+// boundary) with at most Lseq nonzeros.
+__global__ void k_chain_list(const int32_t *__restrict__ row_ptr, int32_t In, int64_t W,
+                             int64_t Lseq, int64_t nnz, int32_t *list, unsigned int *count) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < In;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = row_ptr[r], e = row_ptr[r + 1];
+        if (s < 0 || s >= e || e > nnz || e - s > Lseq) continue;
+        if (s / W == (e - 1) / W) continue;  // inside one tile: the tile kernel runs it
+        list[atomicAdd(count, 1u)] = (int32_t)r;
+    }
+}
+
+// list_ws: 16 bytes of count, then room for one row per tile boundary.
+cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                              int64_t *launches) {
+    g.nchains = (unsigned int *)list_ws;
+    g.chains = (int32_t *)((char *)list_ws + 16);
+    cudaError_t e = cudaMemsetAsync(g.nchains, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const int32_t In = g.a.dims[g.a.n];
+    int64_t blocks = (In + 255) / 256;
+    if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+    if (blocks < 1) blocks = 1;
+    k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.a.nnz, g.chains,
+                                               g.nchains);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+size_t slice_maps_bytes(int64_t ntiles, int J) {
+    return (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * (size_t)(J * J + J) * sizeof(float);
+}
+
 template <typename F>
 static void dispatch_nb(int N, F &&f) {
     // the template argument is the number of other-mode slots (>= N - 1)
@@ -388,6 +422,11 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     const bool with_maps = maps != nullptr;
+    {
+        cudaError_t e = launch_chain_list(g, (char *)maps + slice_maps_bytes(g.ntiles, J), ss.chains,
+                                          sms, launches);
+        if (e != cudaSuccess) return e;
+    }
     if (a.cbf16) {
         if (a.N <= 3) factor_slices_no2_bf16(g, R, J, with_maps, ss, sms, launches);
         else if (a.N <= 4) factor_slices_no3_bf16(g, R, J, with_maps, ss, sms, launches);

@@ -41,6 +41,7 @@ struct sft_ctx {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     int64_t slice_tile = 0;        // 0 = automatic
     int64_t slice_max_direct = 0;  // 0 = automatic
+    int64_t slice_lseq_mode[kMaxOrder] = {};  // per-mode choice of sft_autotune_slices (0 = none)
     std::string last_error;
 };
 
@@ -471,8 +472,10 @@ static int64_t slice_W(const sft_ctx *c, int64_t nnz) {
 // is a dependent sequence of shuffles and FMAs (a few hundred cycles), so
 // chains much longer than a couple of tiles become the pass's tail; measured
 // on the ratings workload, 2 tiles beat both longer chains and maps only.
-static int64_t slice_Lseq(const sft_ctx *c, int64_t W, int64_t nnz) {
+static int64_t slice_Lseq(const sft_ctx *c, int mode, int64_t W, int64_t nnz) {
     (void)nnz;
+    const int64_t tuned = c->slice_lseq_mode[mode];
+    if (tuned != 0) return tuned < 0 ? 0 : tuned;
     if (c->slice_max_direct > 0) return c->slice_max_direct;
     if (c->slice_max_direct < 0) return 0;
     return 2 * W;
@@ -508,8 +511,8 @@ size_t sft_slices_workspace_bytes(const sft_ctx *c, int32_t mode, int64_t nnz) {
     if (!c || mode < 0 || mode >= c->N || nnz < 0) return 0;
     const int64_t W = slice_W(c, nnz);
     const int64_t ntiles = (nnz + W - 1) / W;
-    const int64_t J = c->J[mode];
-    return (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * (size_t)(J * J + J) * sizeof(float);
+    // the piece maps, then the pass's chain list (a count and one row per tile)
+    return slice_maps_bytes(ntiles, c->J[mode]) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 4;
 }
 
 static sft_status check_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
@@ -536,7 +539,7 @@ sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *co
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
-    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, W, nnz), (float *)workspace,
+    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, mode, W, nnz), (float *)workspace,
                                          c->J[mode], c->R, ss, c->sms, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
     return SFT_OK;
@@ -620,7 +623,7 @@ sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *co
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
-    cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, W, nnz), (float *)workspace,
+    cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, mode, W, nnz), (float *)workspace,
                                          fid, fcoord, nfibers, V, c->J[mode], c->R, ss, c->sms,
                                          &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "fiber factor launch");
@@ -659,7 +662,77 @@ sft_status sft_set_slice_tiling(sft_ctx *c, int64_t tile, int64_t max_direct) {
     if (tile < 0) return fail(c, SFT_EINVAL, "tile must be >= 0");
     c->slice_tile = tile;
     c->slice_max_direct = max_direct;  // < 0: every crossing slice goes through maps
+    for (int n = 0; n < kMaxOrder; ++n) c->slice_lseq_mode[n] = 0;
     return SFT_OK;
+}
+
+sft_status sft_autotune_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
+                               const float *sval, const int32_t *row_ptr, int64_t nnz,
+                               const int32_t *fid, const int32_t *const *fcoord, int64_t nfibers,
+                               float *V, float lr, float lambda, void *workspace,
+                               size_t workspace_bytes, void *scratch, size_t scratch_bytes,
+                               int64_t *lseq_out) {
+    if (!c) return SFT_EINVAL;
+    sft_status st = check_slices(c, mode, sidx, sval, row_ptr, nnz);
+    if (st != SFT_OK) return st;
+    const size_t abytes = (size_t)c->dims[mode] * c->J[mode] * sizeof(float);
+    if (!scratch || scratch_bytes < abytes || ((uintptr_t)scratch & 15u))
+        return fail(c, SFT_EINVAL, "scratch missing, misaligned or smaller than I_mode * J_mode floats");
+    if (nnz == 0) return SFT_OK;
+    const bool fibers = fid != nullptr;
+    const int64_t W = slice_W(c, nnz);
+    // candidate limits on the length of a slice run whole (a chain): the
+    // default 2W, powers of two up to 16384, and every crossing slice
+    int64_t cands[10];
+    int nc = 0;
+    cands[nc++] = 2 * W;
+    for (int64_t L = 1024; L <= 16384; L *= 2)
+        if (L > 2 * W) cands[nc++] = L;
+    cands[nc++] = (int64_t)1 << 40;
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+    if (cudaEventCreate(&t1) != cudaSuccess) {
+        cudaEventDestroy(t0);
+        return cuda_fail(c, cudaGetLastError(), "event");
+    }
+    const int64_t keep = c->slice_lseq_mode[mode];
+    cudaError_t e = cudaMemcpyAsync(scratch, c->A[mode], abytes, cudaMemcpyDeviceToDevice, c->stream);
+    float best = -1.f;
+    int64_t best_L = 2 * W;
+    for (int i = 0; i < nc && e == cudaSuccess && st == SFT_OK; ++i) {
+        c->slice_lseq_mode[mode] = cands[i];
+        for (int rep = 0; rep < 2 && st == SFT_OK; ++rep) {  // the second run is timed
+            if (rep == 1) cudaEventRecord(t0, c->stream);
+            st = fibers ? sft_update_factors_fibers(c, mode, sidx, sval, row_ptr, nnz, fid, fcoord,
+                                                    nfibers, V, lr, lambda, workspace,
+                                                    workspace_bytes)
+                        : sft_update_factors_slices(c, mode, sidx, sval, row_ptr, nnz, lr, lambda,
+                                                    workspace, workspace_bytes);
+            if (rep == 1) cudaEventRecord(t1, c->stream);
+            e = cudaMemcpyAsync(c->A[mode], scratch, abytes, cudaMemcpyDeviceToDevice, c->stream);
+        }
+        if (st != SFT_OK || e != cudaSuccess) break;
+        e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && (best < 0.f || ms < best)) {
+            best = ms;
+            best_L = cands[i];
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != SFT_OK) {
+        c->slice_lseq_mode[mode] = keep;
+        return st;
+    }
+    if (e != cudaSuccess) {
+        c->slice_lseq_mode[mode] = keep;
+        return cuda_fail(c, e, "slice autotune");
+    }
+    c->slice_lseq_mode[mode] = best_L;
+    if (lseq_out) *lseq_out = best_L;
+    return read_flag(c);
 }
 
 sft_status sft_sync(sft_ctx *c, int64_t timeout_ms) {

@@ -71,6 +71,7 @@ struct SliceStreams {
 };
 // slice (CSF) layout and the passes over it
 int64_t slice_sort_length(int64_t nnz);
+size_t slice_maps_bytes(int64_t ntiles, int J);
 int slice_tile_length(int64_t nnz, int sms);
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
@@ -156,6 +157,54 @@ template <>
 __device__ __forceinline__ float4 ldC<__nv_bfloat16>(const float *base, int64_t off) {
     const uint2 u = __ldg(reinterpret_cast<const uint2 *>(
         reinterpret_cast<const __nv_bfloat16 *>(base) + off));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+// The raw form of four cached-product entries as loaded (float4, or four
+// bfloat16 in a uint2) and its widening to float; walks keep the raw form in
+// their prefetch rings so that no instruction waits on a gather until the
+// value is used.
+template <typename CT>
+struct CRaw;
+template <>
+struct CRaw<float> {
+    using type = float4;
+};
+template <>
+struct CRaw<__nv_bfloat16> {
+    using type = uint2;
+};
+
+template <typename CT>
+__device__ __forceinline__ typename CRaw<CT>::type ldC_raw(const float *base, int64_t off);
+
+template <>
+__device__ __forceinline__ float4 ldC_raw<float>(const float *base, int64_t off) {
+    return ldg4(base + off);
+}
+
+template <>
+__device__ __forceinline__ uint2 ldC_raw<__nv_bfloat16>(const float *base, int64_t off) {
+    return __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + off));
+}
+
+template <typename CT>
+__device__ __forceinline__ typename CRaw<CT>::type c_one();
+
+template <>
+__device__ __forceinline__ float4 c_one<float>() {
+    return make_float4(1.f, 1.f, 1.f, 1.f);
+}
+
+template <>
+__device__ __forceinline__ uint2 c_one<__nv_bfloat16>() {
+    return make_uint2(0x3f803f80u, 0x3f803f80u);  // four bfloat16 ones
+}
+
+__device__ __forceinline__ float4 widen(const float4 &v) { return v; }
+
+__device__ __forceinline__ float4 widen(const uint2 &u) {
     return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
 }

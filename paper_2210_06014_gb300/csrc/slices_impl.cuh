@@ -38,16 +38,17 @@ __device__ __forceinline__ void load_sample(const PassArgs &a, int64_t t, bool v
     c.x = valid ? __ldg(a.val + t) : 0.f;
 }
 
-template <int NO>
+// The lane's raw entries of every other mode's cached row of one position.
+template <int NO, typename CT>
 struct Rows {
-    float4 r[NO];
+    typename CRaw<CT>::type r[NO];
 };
 
 // Checks the coordinates of a sample (they have arrived by now), reports bad
 // data, and gathers the lane's float4 of every other mode's cached row.
 template <int NO, int R, typename CT, bool WITH_ROW = false>
 __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c, int sub,
-                                          Rows<NO> &w, bool &ok, int32_t &row) {
+                                          Rows<NO, CT> &w, bool &ok, int32_t &row) {
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
@@ -61,15 +62,16 @@ __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c
     ok = c.valid && !bad;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (ok && q < a.N - 1) ? ldC<CT>(a.oC[q], (int64_t)c.i[q] * R + 4 * sub)
-                                     : make_float4(1.f, 1.f, 1.f, 1.f);
+        w.r[q] = (ok && q < a.N - 1) ? ldC_raw<CT>(a.oC[q], (int64_t)c.i[q] * R + 4 * sub)
+                                     : c_one<CT>();
 }
 
-template <int NO>
-__device__ __forceinline__ float4 product(const Rows<NO> &w) {
-    float4 p = w.r[0];
+// prod_q of the rows, widened to float as they are consumed
+template <int NO, typename CT>
+__device__ __forceinline__ float4 product(const Rows<NO, CT> &w) {
+    float4 p = widen(w.r[0]);
 #pragma unroll
-    for (int q = 1; q < NO; ++q) mul4(p, w.r[q]);
+    for (int q = 1; q < NO; ++q) mul4(p, widen(w.r[q]));
     return p;
 }
 
@@ -91,7 +93,7 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
     // coordinates of positions t+D .. t+2D-1 are in flight; a row gather is
     // issued D steps after its coordinates and consumed D steps after that.
     constexpr int D = WalkDepth<NO, DMAX>::value;
-    Rows<NO> ring[D];
+    Rows<NO, CT> ring[D];
     float rx[D];
     bool rok[D];
     int32_t rrow[D];
@@ -113,7 +115,7 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             if (t + u < s1) {
-                body(rrow[u], rx[u], rok[u], product<NO>(ring[u]));
+                body(rrow[u], rx[u], rok[u], product<NO, CT>(ring[u]));
                 // position t + u + D: its coordinates arrived D steps ago
                 load_rows<NO, R, CT, WITH_ROW>(a, cring[u], sub, ring[u], rok[u], rrow[u]);
                 rx[u] = cring[u].x;
@@ -130,6 +132,9 @@ struct SliceArgs {
     int64_t Lseq;            // crossing slices longer than this are split into maps
     int64_t ntiles;
     float *maps;             // [ntiles][2][J*J + J]
+    // crossing slices of at most Lseq nonzeros (built per pass by k_chain_list)
+    int32_t *chains;         // their rows, in no particular order
+    unsigned int *nchains;   // how many
     // fiber-shared v (set for the fiber variant of the factor pass)
     const int32_t *fid;      // fiber of every slice position (-1: bad data)
     const float *V;          // [nfibers][J]: v = B^(n) p of every fiber
@@ -394,8 +399,9 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
     }
 }
 
-// Crossing slices of at most Lseq nonzeros, whole, one per lane group (the
-// group that owns the slice's first tile boundary).
+// Crossing slices of at most Lseq nonzeros, whole, one per lane group: the
+// groups take the slices of the pass's chain list in turn, so every group of
+// every warp has work while the list lasts.
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chains(SliceArgs g) {
     constexpr int T = R / 4;
@@ -406,12 +412,14 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
     const int sub = lane & (T - 1);
     const unsigned m = group_mask<T>(lane);
     const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
-    for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
-         item < g.ntiles - 1; item += groups) {
-        int32_t r;
-        int64_t s, e;
-        if (first_boundary_slice(g, item + 1, r, s, e) && e - s <= g.Lseq)
-            run_direct<FV, NB, R, J, CT>(g, sB, r, s, e, sub, m);
+    const int64_t n = (int64_t)*g.nchains;
+    for (int64_t c = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T; c < n;
+         c += groups) {
+        const int32_t r = __ldg(g.chains + c);
+        if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) continue;
+        const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+        if (!slice_ok(g, s, e)) continue;
+        run_direct<FV, NB, R, J, CT>(g, sB, r, s, e, sub, m);
     }
 }
 
@@ -660,6 +668,7 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
     if (g.ntiles > 1) {
+        // the list holds at most one slice per tile boundary
         const int gch = grid_for(k_slices_chains<FV, NB, R, J, CT>, kSliceThreads, 0, gpb,
                                  g.ntiles - 1, sms);
         k_slices_chains<FV, NB, R, J, CT><<<gch, kSliceThreads, 0, ss.chains>>>(g);
@@ -709,6 +718,8 @@ SFT_SLICE_WRAPPERS(7, bf16)
 SFT_SLICE_WRAPPERS(15, bf16)
 #undef SFT_SLICE_WRAPPERS
 cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms);
+cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                              int64_t *launches);
 // fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
 void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,
                       int sms, int64_t *launches);

@@ -36,7 +36,8 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_sync", "sft_batch_launch_count", "sft_batch_epoch_tasks",
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
-            "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers"]
+            "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers",
+            "sft_autotune_slices"]
 
 
 class SftError(RuntimeError):
@@ -175,6 +176,10 @@ def load(build_if_missing: bool = True):
     lib.sft_update_core_fibers.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, i64, vp,
                                            ctypes.POINTER(vp), i64, vp, f32, f32]
     lib.sft_update_core_fibers.restype = ctypes.c_int
+    lib.sft_autotune_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, vp,
+                                        ctypes.POINTER(vp), i64, vp, f32, f32, vp, ctypes.c_size_t,
+                                        vp, ctypes.c_size_t, ctypes.POINTER(i64)]
+    lib.sft_autotune_slices.restype = ctypes.c_int
     lib.sft_loss_grad_C.argtypes = [ctx, ctypes.POINTER(vp), vp, i64, ctypes.POINTER(vp), i32, vp]
     lib.sft_loss_grad_C.restype = ctypes.c_int
     lib.sft_grad_AB.argtypes = [ctx, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -448,8 +453,12 @@ class Slices:
                        for k in range(len(self.idx))]
         scratch = torch.empty(max(16, sft_fibers_scratch_bytes(self.nnz)), dtype=torch.uint8,
                               device=dev)
-        self.nfibers = sft_group_fibers(dec.ctx, self.mode, self.idx, self.nnz, self.fid,
-                                        self.fcoord, scratch)
+        try:
+            self.nfibers = sft_group_fibers(dec.ctx, self.mode, self.idx, self.nnz, self.fid,
+                                            self.fcoord, scratch)
+        except SftError:
+            self.drop_fibers()
+            raise
         del scratch
         self.V = torch.empty(max(1, self.nfibers), self._J, dtype=torch.float32, device=dev)
         if core is None:
@@ -545,6 +554,28 @@ class Decomposition:
         else:
             sft_update_factors_slices(self.ctx, sl.mode, sl.idx, sl.val, sl.row_ptr, sl.nnz, lr,
                                       lam, ws)
+
+    def autotune_slices(self, sl: Slices, lr=0.01, lam=0.01) -> int:
+        """sft_autotune_slices for the layout's mode; returns the chosen limit on
+        the length of a slice run whole (A is left unchanged)."""
+        lib = load()
+        need = max(16, sft_slices_workspace_bytes(self.ctx, sl.mode, sl.nnz))
+        ws = getattr(self, "_slice_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=sl.val.device)
+            self._slice_ws = ws
+        scratch = torch.empty_like(self.A[sl.mode])
+        out = ctypes.c_int64()
+        fib = sl.fid is not None
+        _check(lib, self.ctx, lib.sft_autotune_slices(
+            self.ctx, int(sl.mode), _ptr_array(sl.idx), _ptr(sl.val), _ptr(sl.row_ptr),
+            int(sl.nnz), _ptr(sl.fid) if fib else None,
+            _ptr_array(sl.fcoord) if fib else None, int(sl.nfibers),
+            _ptr(sl.V) if fib else None, float(lr), float(lam), _ptr(ws),
+            ws.numel() * ws.element_size(), _ptr(scratch),
+            scratch.numel() * scratch.element_size(), ctypes.byref(out)),
+            "sft_autotune_slices")
+        return int(out.value)
 
     def update_core_slices(self, sl: Slices, batch=None, lr=0.01, lam=0.01):
         if sl.fid is not None and sl.P is not None:

@@ -497,3 +497,31 @@ def test_fiber_core_pass_equals_row_pass(sft, case):
         outs.append([b.clone() for b in dec.B])
     for n, (a, b) in enumerate(zip(*outs)):
         assert torch.equal(a, b), (case, n, (a - b).abs().max().item())
+
+
+@pytest.mark.parametrize("fibers", [False, True])
+def test_slice_autotune_leaves_A_and_keeps_parity(sft, oracle_mod, skewed, fibers):
+    """sft_autotune_slices restores A^(n) after its trials, returns one of its
+    candidates, and the pass it selects still equals the sequential oracle."""
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        sl = dec.slices(n, idx, val, None)
+        if fibers:
+            sl.build_fibers(dec)
+        A0 = dec.A[n].clone()
+        L = dec.autotune_slices(sl, lr=0.01, lam=0.01)
+        dec.sync(60_000)
+        assert torch.equal(dec.A[n], A0)
+        W = max(32, min(2048, T.nnz // (torch.cuda.get_device_properties(0).multi_processor_count * 2048)))
+        assert L == 2 * W or L in (1024, 2048, 4096, 8192, 16384, 1 << 40)
+        dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+        dec.sync(60_000)
+        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        A0n = A0.cpu().numpy().astype(np.float64)
+        assert rel_fro(got - A0n, ref.A[n] - A0n) < 1e-4, n
+        assert rel_fro(got, ref.A[n]) < TOL32, n
