@@ -65,9 +65,9 @@ typedef enum {
 typedef enum {
     SFT_FP32 = 0, /* A, B, C float32 */
     SFT_BF16 = 1  /* C stored as bfloat16 (rounded to nearest even by sft_refresh_C);
-                     A and B stay float32 and all arithmetic is float32.  Supported by
-                     the slice calls, sft_refresh_C, sft_loss and sft_predict; the COO
-                     update calls return SFT_ENOTSUP. */
+                     A and B stay float32 (master copies).  The gathers widen C to
+                     float32; the refresh and the COO core gradient run on tensor
+                     cores (see sft_set_tensor_cores), everything else in float32. */
 } sft_precision;
 
 typedef struct {
@@ -286,6 +286,22 @@ sft_status sft_update_core_fibers(sft_ctx *ctx, int32_t mode, const int32_t *con
  * crossing slice is split into maps).  Results do not depend on it beyond
  * rounding. */
 sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
+
+/* Tensor cores for the two dense contractions when the cached products are
+ * bfloat16 (SFT_BF16); on by default.  With enable != 0:
+ *   sft_refresh_C (J_n in {8, 16, 32}, R in {16, 32}): C^(n) = A^(n) B^(n) by
+ *     tcgen05 MMAs of kind tf32 (tiles of A^(n) copied by TMA; float32
+ *     accumulation; C^(n) rounded to bfloat16 as before);
+ *   sft_update_core (R in {16, 32}): the minibatch core gradient
+ *     G = sum_s e_s a p_s^T of Eq. (11) as the contraction (J_n x M).(M x R) by
+ *     tcgen05 MMAs of kind f16 with bfloat16 operands e_s a and p_s and a
+ *     float32 accumulator per block; the block partials are summed in float64
+ *     in a fixed order, as on the CUDA-core path.
+ * With enable = 0 (or other shapes) the float32 CUDA-core kernels run.  The
+ * float32 configuration (SFT_FP32) never uses tensor cores.  A wait of a
+ * tensor-core kernel that runs out (2 s) is reported as SFT_ETIMEOUT by the
+ * next sft_sync / sft_loss. */
+sft_status sft_set_tensor_cores(sft_ctx *ctx, int32_t enable);
 
 /* Per-mode autotuner of the slice factor pass: times the pass of `mode` with
  * several limits on the length of a crossing slice that is run whole as one

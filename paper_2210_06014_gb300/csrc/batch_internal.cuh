@@ -64,7 +64,7 @@ struct BatchArgs {
     int64_t wait_limit;     // polls before a wait gives up
 };
 
-constexpr int kErrWait = 4;  // a dependency wait ran out of polls
+// kErrWait (sft_internal.cuh): a dependency wait ran out of polls
 
 cudaError_t launch_batch(const BatchArgs &g, bool cbf16, int grid, cudaStream_t st);
 int batch_blocks_per_sm(bool cbf16);

@@ -14,9 +14,9 @@
 // Kernel 2 (k_core_apply): sums the block partials in block order (float64)
 // and applies B += lr (G / M_b - lambda B).
 //
-// G is small (at most 32 x 32) and K = M is a stream of gathered rows, so the
-// contraction rides along the HBM-bound gather instead of going to a tensor-
-// core GEMM.
+// This CUDA-core form is exact in float32 (the float32 parity mode).  With
+// bfloat16 cached products and R in {16, 32}, sft_update_core uses the
+// tensor-core form of the same contraction instead (k_core_grad_tc, k_tc.cu).
 #include "dispatch.cuh"
 #include "sft_internal.cuh"
 
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(kCoreThreads) k_core_grad(PassArgs a, float *_
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = k0 + u;
-                    c[u] = (ok && k < a.N && k != a.n) ? ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub)
+                    c[u] = (ok && k < a.N && k != a.n) ? (a.cbf16 ? ldC<__nv_bfloat16>(a.C[k], (int64_t)ik[k] * R + 4 * sub)
+                                                              : ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub))
                                                        : make_float4(1.f, 1.f, 1.f, 1.f);
                 }
 #pragma unroll

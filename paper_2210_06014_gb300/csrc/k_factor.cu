@@ -43,7 +43,8 @@ __device__ __forceinline__ float4 hadamard_others(const PassArgs &a, const int32
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int k = k0 + u;
-                c[u] = (ok && k < a.N && k != a.n) ? ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub)
+                c[u] = (ok && k < a.N && k != a.n) ? (a.cbf16 ? ldC<__nv_bfloat16>(a.C[k], (int64_t)ik[k] * R + 4 * sub)
+                                                              : ldg4(a.C[k] + (int64_t)ik[k] * R + 4 * sub))
                                                    : make_float4(1.f, 1.f, 1.f, 1.f);
             }
 #pragma unroll

@@ -42,6 +42,7 @@ struct sft_ctx {
     int64_t slice_tile = 0;        // 0 = automatic
     int64_t slice_max_direct = 0;  // 0 = automatic
     int64_t slice_lseq_mode[kMaxOrder] = {};  // per-mode choice of sft_autotune_slices (0 = none)
+    int tensor_cores = 1;  // tcgen05 refresh / core gradient for bfloat16 cached products
     std::string last_error;
 };
 
@@ -263,8 +264,13 @@ sft_status sft_refresh_C(sft_ctx *c, int32_t mode) {
     if (mode < -1 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
     for (int n = 0; n < c->N; ++n) {
         if (mode >= 0 && n != mode) continue;
-        cudaError_t e = launch_refresh(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R,
-                                       c->cbf16 != 0, c->stream, c->sms);
+        cudaError_t e;
+        if (c->cbf16 && c->tensor_cores && refresh_tc_supported(c->J[n], c->R))
+            e = launch_refresh_tc(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R, c->err,
+                                  c->stream, c->sms);
+        else
+            e = launch_refresh(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R,
+                               c->cbf16 != 0, c->stream, c->sms);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(c, e, "refresh launch");
     }
@@ -279,9 +285,6 @@ sft_status sft_update_factors(sft_ctx *c, int32_t mode, const int32_t *const *id
     sft_status st = check_set(c, idx, val, nnz);
     if (st != SFT_OK) return st;
     if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
-    if (c->cbf16)
-        return fail(c, SFT_ENOTSUP, "the COO factor pass needs float32 cached products; use the "
-                                    "slice calls with SFT_BF16");
     if (nnz == 0) return SFT_OK;
     PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
     if (!c->deterministic) {
@@ -313,9 +316,6 @@ sft_status sft_update_core(sft_ctx *c, int32_t mode, const int32_t *const *idx, 
     if (st != SFT_OK) return st;
     if (!std::isfinite(lr) || !std::isfinite(lambda)) return fail(c, SFT_EINVAL, "lr / lambda not finite");
     if (batch < 1) return fail(c, SFT_EINVAL, "batch must be >= 1");
-    if (c->cbf16)
-        return fail(c, SFT_ENOTSUP, "the COO core pass needs float32 cached products; use the "
-                                    "slice calls with SFT_BF16");
     if (nnz == 0) return SFT_OK;
     PassArgs a = pass_args(c, mode, idx, val, perm, nnz, lr, lambda);
     for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
@@ -323,7 +323,9 @@ sft_status sft_update_core(sft_ctx *c, int32_t mode, const int32_t *const *idx, 
         a.count = nnz - b0 < batch ? nnz - b0 : batch;
         int nblk = core_blocks_for(a.count, c->sms);
         if (nblk > c->core_max_blocks) nblk = c->core_max_blocks;
-        cudaError_t e = launch_core(a, c->J[mode], c->R, c->core_partials, nblk, c->stream);
+        const bool tc = c->cbf16 && c->tensor_cores && core_tc_supported(c->J[mode], c->R);
+        cudaError_t e = tc ? launch_core_tc(a, c->J[mode], c->R, c->core_partials, nblk, c->stream)
+                           : launch_core(a, c->J[mode], c->R, c->core_partials, nblk, c->stream);
         c->launches += 2;
         if (e != cudaSuccess) return cuda_fail(c, e, "core launch");
     }
@@ -354,6 +356,10 @@ static sft_status read_flag(sft_ctx *c) {
         std::string m = "a kernel skipped bad data:";
         if (flag & kErrIndex) m += " coordinate out of range;";
         if (flag & kErrPerm) m += " permutation entry >= nnz;";
+        if (flag & kErrWait) {
+            m += " a tensor-core kernel gave up waiting for its copies / MMAs;";
+            return fail(c, SFT_ETIMEOUT, m);
+        }
         return fail(c, SFT_EINVAL, m);
     }
     return SFT_OK;
@@ -663,6 +669,12 @@ sft_status sft_set_slice_tiling(sft_ctx *c, int64_t tile, int64_t max_direct) {
     c->slice_tile = tile;
     c->slice_max_direct = max_direct;  // < 0: every crossing slice goes through maps
     for (int n = 0; n < kMaxOrder; ++n) c->slice_lseq_mode[n] = 0;
+    return SFT_OK;
+}
+
+sft_status sft_set_tensor_cores(sft_ctx *c, int32_t enable) {
+    if (!c) return SFT_EINVAL;
+    c->tensor_cores = enable ? 1 : 0;
     return SFT_OK;
 }
 

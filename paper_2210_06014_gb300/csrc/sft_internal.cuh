@@ -16,6 +16,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Error flag bits raised by kernels (device int in the workspace).
 constexpr int kErrIndex = 1;  // coordinate out of range
 constexpr int kErrPerm = 2;   // permutation entry >= nnz
+constexpr int kErrWait = 4;   // a bounded wait ran out (tensor-core kernels, batched runner)
 
 // Operands of one pass over the nonzeros of mode n.
 struct PassArgs {
@@ -61,6 +62,14 @@ cudaError_t launch_factor_det(const PassArgs &a, int J, int R, const DetFactorWs
 cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nblk,
                         cudaStream_t st);
 int core_blocks_for(int64_t count, int sms);
+// tensor-core (tcgen05) forms of the refresh and the minibatch core gradient
+// for bfloat16 cached products (k_tc.cu)
+bool refresh_tc_supported(int J, int R);
+cudaError_t launch_refresh_tc(const float *A, const float *B, void *C, int64_t I, int J, int R,
+                              int *err, cudaStream_t st, int sms);
+bool core_tc_supported(int J, int R);
+cudaError_t launch_core_tc(const PassArgs &a, int J, int R, float *partials, int nblk,
+                           cudaStream_t st);
 cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
                               float lr, float lam, cudaStream_t st);
 // Streams of one slice factor pass: `tiles` is the caller's stream; `chains`

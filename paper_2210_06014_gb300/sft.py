@@ -37,7 +37,7 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
             "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers",
-            "sft_autotune_slices"]
+            "sft_autotune_slices", "sft_set_tensor_cores"]
 
 
 class SftError(RuntimeError):
@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True):
     lib.sft_update_core_slices.restype = ctypes.c_int
     lib.sft_set_slice_tiling.argtypes = [ctx, i64, i64]
     lib.sft_set_slice_tiling.restype = ctypes.c_int
+    lib.sft_set_tensor_cores.argtypes = [ctx, i32]
+    lib.sft_set_tensor_cores.restype = ctypes.c_int
     lib.sft_update_factors_noalloc.argtypes = [
         i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
         ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
@@ -351,6 +353,11 @@ def sft_set_slice_tiling(ctx, tile: int = 0, max_direct: int = 0) -> None:
            "sft_set_slice_tiling")
 
 
+def sft_set_tensor_cores(ctx, enable: bool = True) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_set_tensor_cores(ctx, 1 if enable else 0), "sft_set_tensor_cores")
+
+
 def sft_update_factors_noalloc(dims, J, R, mode, A_mode, B_mode, C, idx, val, perm, nnz, batch,
                                lr, lam, stream=None) -> int:
     """The allocation-free factor pass; returns the sft_status code."""
@@ -481,11 +488,14 @@ class Decomposition:
     A[n] (I_n x J_n) and B[n] (J_n x R) are float32 torch tensors on the current
     CUDA device; C[n] = A[n] B[n] (I_n x R) is float32, or bfloat16 with
     prec = SFT_BF16; ``workspace`` is a byte tensor sized by
-    sft_workspace_bytes.  All methods forward to the C ABI."""
+    sft_workspace_bytes.  ``tensor_cores`` selects the tcgen05 refresh and core
+    gradient for bfloat16 C (sft_set_tensor_cores).  All methods forward to the
+    C ABI."""
 
     def __init__(self, A0: Sequence[torch.Tensor], B0: Sequence[torch.Tensor],
                  deterministic: bool = True, max_batch: int = 4096, device="cuda",
-                 stream=None, prec: int = SFT_FP32, copy: bool = True):
+                 stream=None, prec: int = SFT_FP32, copy: bool = True,
+                 tensor_cores: bool = True):
         if copy:
             self.A = [a.to(device=device, dtype=torch.float32).contiguous().clone() for a in A0]
             self.B = [b.to(device=device, dtype=torch.float32).contiguous().clone() for b in B0]
@@ -509,6 +519,7 @@ class Decomposition:
             raise SftError(SFT_EINVAL, "sft_workspace_bytes rejected the configuration")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.ctx = sft_init(self.cfg, self.A, self.B, self.C, self.workspace)
+        sft_set_tensor_cores(self.ctx, tensor_cores)
         sft_refresh_C(self.ctx, -1)
 
     def close(self):
