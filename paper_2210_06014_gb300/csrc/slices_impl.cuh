@@ -425,13 +425,18 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
 
 // ============================================================================ factor: long slices
 // Composes the steps of positions [s0, s1) of one slice into the affine map
-// (M, c) with a_after = M a_before + c.  The lane holds rows [sub*JL, ...) of M
-// and c.
+// (M, c) with a_after = M a_before + c.  The lane holds columns
+// [sub*JC, (sub+1)*JC) of M (all J rows) and rows [sub*JL, (sub+1)*JL) of c.
+// The walk hands each lane its J/T entries of v; an all-gather over the group
+// (exact copies, independent of M) gives the whole v, so the M recurrence
+// (w = v^T M on the lane's columns, then the rank-1 update) needs no
+// cross-lane reduction; only v . c is summed over the group.
 template <bool FV, int NB, int R, int J, typename CT>
 __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, int64_t s0,
                                             int64_t s1, int sub, unsigned m, float *out) {
     constexpr int T = R / 4;
-    constexpr int JL = J / T;
+    constexpr int JL = J / T;  // entries of v and rows of c per lane
+    constexpr int JC = J / T;  // columns of M per lane
     const PassArgs &a = g.a;
     // The map is kept as M = alpha^n M', c = alpha^n c' (n = steps since the
     // last fold), so one step is a pure rank-1 FFMA update:
@@ -443,20 +448,22 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     const float nvc = -a.lr * ainv;
     float apow = 1.f, pw = ainv;
     int since = 0;
-    float M[JL][J], cv[JL];
+    float M[J][JC], cv[JL];
 #pragma unroll
-    for (int q = 0; q < JL; ++q) {
-        cv[q] = 0.f;
+    for (int q = 0; q < J; ++q) {
 #pragma unroll
-        for (int k = 0; k < J; ++k) M[q][k] = (sub * JL + q == k) ? 1.f : 0.f;
+        for (int k = 0; k < JC; ++k) M[q][k] = (sub * JC + k == q) ? 1.f : 0.f;
     }
+#pragma unroll
+    for (int q = 0; q < JL; ++q) cv[q] = 0.f;
     auto fold = [&]() {
 #pragma unroll
-        for (int q = 0; q < JL; ++q) {
+        for (int q = 0; q < J; ++q) {
 #pragma unroll
-            for (int k = 0; k < J; ++k) M[q][k] *= apow;
-            cv[q] *= apow;
+            for (int k = 0; k < JC; ++k) M[q][k] *= apow;
         }
+#pragma unroll
+        for (int q = 0; q < JL; ++q) cv[q] *= apow;
         apow = 1.f;
         pw = ainv;
         since = 0;
@@ -467,30 +474,38 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     float xq = 0.f;
     bool okq = false, have = false;
     auto apply = [&]() {
-        // w = v^T M' (all J columns), s = v . c'
-        float w[J];
+        float v[J];
 #pragma unroll
-        for (int k = 0; k < J; ++k) {
-            float acc = 0.f;
+        for (int s = 0; s < T; ++s) {
 #pragma unroll
-            for (int q = 0; q < JL; ++q) acc = fmaf(vq[q], M[q][k], acc);
-            w[k] = acc;
+            for (int q = 0; q < JL; ++q) v[s * JL + q] = __shfl_sync(m, vq[q], s, T);
+        }
+        // w = v^T M' on the lane's columns (two partial sums each)
+        float w[JC];
+#pragma unroll
+        for (int k = 0; k < JC; ++k) {
+            float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < J; q += 2) {
+                e0 = fmaf(v[q], M[q][k], e0);
+                e1 = fmaf(v[q + 1], M[q + 1][k], e1);
+            }
+            w[k] = e0 + e1;
         }
         float sc = 0.f;
 #pragma unroll
         for (int q = 0; q < JL; ++q) sc = fmaf(vq[q], cv[q], sc);
-#pragma unroll
-        for (int k = 0; k < J; ++k) w[k] = group_sum_m<T>(w[k], m);
         sc = group_sum_m<T>(sc, m);
         if (okq) {
             const float xs = a.lr * xq * pw;
 #pragma unroll
-            for (int q = 0; q < JL; ++q) {
-                const float nv = nvc * vq[q];
+            for (int q = 0; q < J; ++q) {
+                const float nv = nvc * v[q];
 #pragma unroll
-                for (int k = 0; k < J; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
-                cv[q] = fmaf(xs, vq[q], fmaf(nv, sc, cv[q]));
+                for (int k = 0; k < JC; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
             }
+#pragma unroll
+            for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vq[q], fmaf(nvc * vq[q], sc, cv[q]));
             apow *= alpha;
             pw *= ainv;
             if (++since == 16) fold();
@@ -510,7 +525,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     if (have) apply();
     fold();
 #pragma unroll
-    for (int q = 0; q < JL; ++q) store_run<J>(out + (sub * JL + q) * J, M[q]);
+    for (int q = 0; q < J; ++q) store_run<JC>(out + q * J + sub * JC, M[q]);
     store_run<JL>(out + J * J + sub * JL, cv);
 }
 
