@@ -158,8 +158,10 @@ __global__ void k_core_apply(float *__restrict__ B, const float *__restrict__ pa
     B[q] = (float)(bq + (double)lr * (g / (double)Mb - (double)lam * bq));
 }
 
+// One block per 128 nonzeros (a 4096-nonzero minibatch spreads over 32 SMs),
+// at most four per SM (a whole pass).
 int core_blocks_for(int64_t count, int sms) {
-    int64_t b = (count + 511) / 512;
+    int64_t b = (count + 127) / 128;
     const int64_t cap = (int64_t)sms * 4;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
