@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 import torch  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "dram_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -144,6 +145,30 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+
+
+def source_digest(paths) -> str:
+    """sha256 over the bytes of the given repository files, in the given order."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(key: str):
+    """DRAM bytes (read + write) per launch of a timed unit, from the committed
+    record of an ncu capture (profiles/dram_traffic.json), or None when there is
+    no record for `key` or the kernels' sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            rec = json.load(f)[key]
+        if source_digest(rec["sources"]) != rec["digest"]:
+            return None
+        return float(rec["bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
 
 
 def peaks():
@@ -915,7 +940,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "achieved_gbs": {k: v[1] for k, v in kernels.items()},
             },
             "roofline": {"bound": "hbm", "kernel": f"{dom} pass", "achieved": ach, "peak": peak,
-                         "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "unit": "GB/s", "frac": ach / peak,
+                         "traffic": measured_traffic(f"{workload}|{args.prec}|{args.path}|{dom}"),
                          "peak_source": peak_kind},
             "clocks": clk.summary(),
             "gpu_launches": launches,

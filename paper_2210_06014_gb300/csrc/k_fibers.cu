@@ -145,14 +145,16 @@ __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci
 }
 
 // V[f] = B^(n) prod_{k != n} C^(k)[i_k(f)] for every fiber; T = R/4 lanes per
-// fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  The next fiber's
-// coordinates are loaded one iteration ahead.
-template <int R, int J, typename CT>
+// fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  NO bounds the
+// number of other modes.  The next fiber's coordinates are loaded one
+// iteration ahead and, for NO <= 3, its cached rows as well (they are in
+// flight while the current fiber's v is formed).
+template <int R, int J, typename CT, int NO>
 __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords fc,
                                                          int64_t nfibers, float *V) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
-    constexpr int NO = kMaxOrder - 1;
+    constexpr bool PIPE = NO <= 3;
     __shared__ __align__(16) float sB[J * R];
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = a.B[q];
     __syncthreads();
@@ -167,15 +169,7 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords
 #pragma unroll
         for (int q = 0; q < NO; ++q) nc[q] = (f < nfibers && q < a.N - 1) ? __ldg(fc.c[q] + f) : 0;
     };
-    fetch(first);
-    for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
-        const int64_t f = f0 + lane / T;
-        int32_t ci[NO];
-#pragma unroll
-        for (int q = 0; q < NO; ++q) ci[q] = nc[q];
-        fetch(f + stride);
-        Rows<NO, CT> w;
-        const bool ok = fiber_rows<R, CT, NO>(a, ci, f < nfibers, sub, w);
+    auto emit = [&](int64_t f, bool ok, const Rows<NO, CT> &w) {
         const float4 p = product<NO, CT>(w);
         float vp[J];
 #pragma unroll
@@ -188,6 +182,41 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords
 #pragma unroll
         for (int q = 0; q < JL; ++q) vq[q] = vp[q];
         if (ok) store_run<JL>(V + f * J + sub * JL, vq);
+    };
+    fetch(first);
+    if constexpr (PIPE) {
+        Rows<NO, CT> w;
+        bool ok;
+        {
+            int32_t ci[NO];
+#pragma unroll
+            for (int q = 0; q < NO; ++q) ci[q] = nc[q];
+            fetch(first + stride);
+            ok = fiber_rows<R, CT, NO>(a, ci, first < nfibers, sub, w);
+        }
+        for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
+            const int64_t f = f0 + lane / T;
+            int32_t ci[NO];
+#pragma unroll
+            for (int q = 0; q < NO; ++q) ci[q] = nc[q];
+            fetch(f + 2 * stride);
+            Rows<NO, CT> wn;
+            const bool okn = fiber_rows<R, CT, NO>(a, ci, f + stride < nfibers, sub, wn);
+            emit(f, ok, w);
+            w = wn;
+            ok = okn;
+        }
+    } else {
+        for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
+            const int64_t f = f0 + lane / T;
+            int32_t ci[NO];
+#pragma unroll
+            for (int q = 0; q < NO; ++q) ci[q] = nc[q];
+            fetch(f + stride);
+            Rows<NO, CT> w;
+            const bool ok = fiber_rows<R, CT, NO>(a, ci, f < nfibers, sub, w);
+            emit(f, ok, w);
+        }
     }
 }
 
@@ -289,10 +318,16 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
         const int64_t per_block = kFibThreads / (R / 4);
         int64_t blocks = (nfibers + per_block - 1) / per_block;
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-        if (a.cbf16)
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, V)));
+        const FiberCoords fc = fiber_coords(a, fcoord);
+        constexpr int NG = kMaxOrder - 1;
+        if (a.cbf16 && a.N <= 3)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16, 2><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+        else if (a.cbf16)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16, NG><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+        else if (a.N <= 3)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, 2><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         else
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fiber_coords(a, fcoord), nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, NG><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         *launches += 1;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -13,6 +13,9 @@
 #define SFT_DIRECT_MINB 2
 #define SFT_MAPS_MINB (J >= 32 ? 1 : 2)
 #define SFT_CORE_MINB (J >= 32 ? 2 : 4)
+#ifndef SFT_MAP_RING_D
+#define SFT_MAP_RING_D 4
+#endif
 
 namespace sft {
 
@@ -424,16 +427,124 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
 }
 
 // ============================================================================ factor: long slices
+// Shared-memory prefetch ring of the fiber-shared v for the map walk: D slots
+// of J floats per lane group.  Lane `sub` copies its J/T floats of a row with
+// cp.async P = D - 1 positions ahead of their use (one commit group per step),
+// the fiber id of a position is loaded D steps before its copy is issued and
+// the value D steps before it is used, so no step waits on memory.  A slot is
+// refilled one step after it was read; the __syncwarp at the top of every step
+// orders the group's reads of a slot before its refill.
+template <int R, int J>
+struct MapRing {
+    static constexpr int GPB = 256 / (R / 4);  // lane groups per block of the map kernel
+    static constexpr int DMAX = SFT_MAP_RING_D;
+    static constexpr int D = GPB * DMAX * J * 4 <= 32768 ? DMAX : 2;
+    static constexpr bool use = GPB * D * J * 4 <= 32768;  // else the register walk
+};
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(float *dst, const float *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (BYTES >= 16) {
+#pragma unroll
+        for (int q = 0; q < BYTES / 16; ++q)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * q),
+                         "l"(src + 4 * q)
+                         : "memory");
+    } else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+
+// Calls step(v, vl, x, ok) for slice positions [s0, s1) in order: v = all J
+// entries of the position's fiber v (shared memory), vl = the lane's J/T.
+template <int R, int J, typename Step>
+__device__ __forceinline__ void walk_v_ring(const SliceArgs &g, float *ring, int64_t s0, int64_t s1,
+                                            int sub, unsigned m, Step &&step) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int D = MapRing<R, J>::D;
+    constexpr int P = D - 1;
+    const PassArgs &a = g.a;
+    const int64_t n = s1 - s0;
+    int32_t fr[D];     // fiber ids, slot q % D holds position q until its copy is issued
+    float xr[D];       // values, slot q % D holds position q until it is used
+    uint32_t okm = 0;  // bit q % D: position q is valid
+    auto issue = [&](int64_t q, int32_t f) {  // copy v of position q into slot q % D
+        const bool valid = q < n;
+        const bool good = (uint64_t)(int64_t)f < (uint64_t)g.nfibers;
+        if (valid && !good) atomicOr(a.err, kErrIndex);
+        const int slot = (int)(q % D);
+        okm = (okm & ~(1u << slot)) | ((valid && good) ? (1u << slot) : 0u);
+        if (valid && good) cp_async<JL * 4>(ring + slot * J + sub * JL, g.V + (int64_t)f * J + sub * JL);
+        cp_async_commit();
+    };
+    auto ld_fid = [&](int64_t q) { return q < n ? __ldg(g.fid + s0 + q) : -1; };
+    auto ld_x = [&](int64_t q) { return q < n ? __ldg(a.val + s0 + q) : 0.f; };
+    // prologue: copies of positions 0 .. P-1, fiber ids of P .. P+D-1, values of 0 .. D-1
+    {
+        int32_t f0[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) f0[q] = ld_fid(q);
+#pragma unroll
+        for (int q = 0; q < D; ++q) fr[(P + q) % D] = ld_fid(P + q);
+#pragma unroll
+        for (int q = 0; q < D; ++q) xr[q] = ld_x(q);
+#pragma unroll
+        for (int q = 0; q < P; ++q) issue(q, f0[q]);
+    }
+    for (int64_t b = 0; b < n; b += D) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            const int64_t i = b + u;
+            if (i < n) {  // uniform over the group
+                cp_async_wait<P - 1>();  // this lane's copy of position i has landed
+                __syncwarp(m);           // ... and every lane's; slot (i-1) % D is free
+                const int sq = (u + P) % D;  // slot of position i + P (static)
+                issue(i + P, fr[sq]);
+                fr[sq] = ld_fid(i + P + D);
+                float v[J], vl[JL];
+                const float *src = ring + u * J;  // slot i % D == u (b is a multiple of D)
+#pragma unroll
+                for (int q = 0; q < J; q += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
+                    v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < JL; ++q) vl[q] = src[sub * JL + q];
+                const float x = xr[u];
+                const bool ok = (okm >> u) & 1u;
+                xr[u] = ld_x(i + D);
+                step(v, vl, x, ok);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp(m);
+}
+
 // Composes the steps of positions [s0, s1) of one slice into the affine map
 // (M, c) with a_after = M a_before + c.  The lane holds columns
 // [sub*JC, (sub+1)*JC) of M (all J rows) and rows [sub*JL, (sub+1)*JL) of c.
-// The walk hands each lane its J/T entries of v; an all-gather over the group
-// (exact copies, independent of M) gives the whole v, so the M recurrence
+// Every lane has the whole v of a step (read from the shared-memory ring in
+// the fiber variant; all-gathered over the group from the walk's J/T entries
+// otherwise: exact copies either way, independent of M), so the M recurrence
 // (w = v^T M on the lane's columns, then the rank-1 update) needs no
-// cross-lane reduction; only v . c is summed over the group.
+// cross-lane reduction; only v . c is summed over the group.  The arithmetic
+// is the same in both variants, so their results are bitwise equal.
 template <bool FV, int NB, int R, int J, typename CT>
-__device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, int64_t s0,
-                                            int64_t s1, int sub, unsigned m, float *out) {
+__device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB, float *ring,
+                                            int64_t s0, int64_t s1, int sub, unsigned m,
+                                            float *out) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;  // entries of v and rows of c per lane
     constexpr int JC = J / T;  // columns of M per lane
@@ -468,18 +579,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         pw = ainv;
         since = 0;
     };
-    // One-step software pipeline: v of position t (independent of M) is
-    // computed while the rank-1 update of position t-1 is applied.
-    float vq[JL];
-    float xq = 0.f;
-    bool okq = false, have = false;
-    auto apply = [&]() {
-        float v[J];
-#pragma unroll
-        for (int s = 0; s < T; ++s) {
-#pragma unroll
-            for (int q = 0; q < JL; ++q) v[s * JL + q] = __shfl_sync(m, vq[q], s, T);
-        }
+    auto apply = [&](const float (&v)[J], const float (&vl)[JL], float x, bool ok) {
         // w = v^T M' on the lane's columns (two partial sums each)
         float w[JC];
 #pragma unroll
@@ -494,10 +594,10 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         }
         float sc = 0.f;
 #pragma unroll
-        for (int q = 0; q < JL; ++q) sc = fmaf(vq[q], cv[q], sc);
+        for (int q = 0; q < JL; ++q) sc = fmaf(vl[q], cv[q], sc);
         sc = group_sum_m<T>(sc, m);
-        if (okq) {
-            const float xs = a.lr * xq * pw;
+        if (ok) {
+            const float xs = a.lr * x * pw;
 #pragma unroll
             for (int q = 0; q < J; ++q) {
                 const float nv = nvc * v[q];
@@ -505,24 +605,43 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
                 for (int k = 0; k < JC; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
             }
 #pragma unroll
-            for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vq[q], fmaf(nvc * vq[q], sc, cv[q]));
+            for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vl[q], fmaf(nvc * vl[q], sc, cv[q]));
             apow *= alpha;
             pw *= ainv;
             if (++since == 16) fold();
         }
     };
-    // prefetch depth 1: with the pipelined step a deeper ring spills at the
-    // 128-register bound (measured on both paths)
-    walk_steps<FV, NB, R, J, CT, 1, false>(g, sB, s0, s1, sub, m,
-                                           [&](int32_t, float x0, bool ok0, const float (&v)[JL]) {
-        if (have) apply();
+    if constexpr (FV && MapRing<R, J>::use) {
+        walk_v_ring<R, J>(g, ring, s0, s1, sub, m, apply);
+    } else {
+        // One-step software pipeline: v of position t (independent of M) is
+        // computed while the rank-1 update of position t-1 is applied.
+        float vq[JL];
+        float xq = 0.f;
+        bool okq = false, have = false;
+        auto gathered = [&]() {
+            float v[J];
 #pragma unroll
-        for (int q = 0; q < JL; ++q) vq[q] = v[q];
-        xq = x0;
-        okq = ok0;
-        have = true;
-    });
-    if (have) apply();
+            for (int s = 0; s < T; ++s) {
+#pragma unroll
+                for (int q = 0; q < JL; ++q) v[s * JL + q] = __shfl_sync(m, vq[q], s, T);
+            }
+            apply(v, vq, xq, okq);
+        };
+        // prefetch depth 1: with the pipelined step a deeper ring spills at the
+        // 128-register bound (measured)
+        walk_steps<FV, NB, R, J, CT, 1, false>(g, sB, s0, s1, sub, m,
+                                                  [&](int32_t, float x0, bool ok0,
+                                                      const float (&v)[JL]) {
+            if (have) gathered();
+#pragma unroll
+            for (int q = 0; q < JL; ++q) vq[q] = v[q];
+            xq = x0;
+            okq = ok0;
+            have = true;
+        });
+        if (have) gathered();
+    }
     fold();
 #pragma unroll
     for (int q = 0; q < J; ++q) store_run<JC>(out + q * J + sub * JC, M[q]);
@@ -535,15 +654,20 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
+    constexpr int GPB = kSliceThreads / T;
+    constexpr bool RINGED = FV && MapRing<R, J>::use;
+    constexpr int RING = RINGED ? GPB * MapRing<R, J>::D * J : 4;  // v prefetch rings
     __shared__ __align__(16) float sB[J * R];
+    __shared__ __align__(16) float sring[RING];
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int sub = lane & (T - 1);
     const unsigned m = group_mask<T>(lane);
-    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
+    float *ring = RINGED ? sring + (threadIdx.x / T) * (MapRing<R, J>::D * J) : nullptr;
+    const int64_t groups = (int64_t)gridDim.x * GPB;
     const int32_t *rowidx = g.a.idx[g.a.n];
-    for (int64_t t = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T; t < g.ntiles;
+    for (int64_t t = (int64_t)blockIdx.x * GPB + threadIdx.x / T; t < g.ntiles;
          t += groups) {
         const int64_t p0 = t * g.W;
         const int64_t p1 = min(g.a.nnz, p0 + g.W);
@@ -561,10 +685,10 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
             // slot 0: run that started before the tile; slot 1: run that starts in
             // the tile and continues after it
             if (side == 0 && before) {
-                compose_map<FV, NB, R, J, CT>(g, sB, p0, min(e, p1), sub, m,
+                compose_map<FV, NB, R, J, CT>(g, sB, ring, p0, min(e, p1), sub, m,
                                       g.maps + (t * 2 + 0) * (int64_t)(J * J + J));
             } else if (side == 1 && after && !before) {
-                compose_map<FV, NB, R, J, CT>(g, sB, max(s, p0), p1, sub, m,
+                compose_map<FV, NB, R, J, CT>(g, sB, ring, max(s, p0), p1, sub, m,
                                       g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
             }
         }
