@@ -146,11 +146,12 @@ __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci
 
 // V[f] = B^(n) prod_{k != n} C^(k)[i_k(f)] for every fiber; T = R/4 lanes per
 // fiber, lane `sub` writes entries [sub*J/T, (sub+1)*J/T).  NO bounds the
-// number of other modes.  The next fiber's coordinates are loaded one
-// iteration ahead and, for NO <= 3, its cached rows as well (they are in
-// flight while the current fiber's v is formed).
+// number of other modes.  For NO <= 3 a group forms two fibers' v per
+// iteration (f and f + stride: each float4 of B read from shared memory serves
+// both) while the next pair's coordinates and cached rows are in flight;
+// otherwise one fiber per iteration, its coordinates loaded one ahead.
 template <int R, int J, typename CT, int NO>
-__global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords fc,
+__global__ void __launch_bounds__(kFibThreads, (NO <= 3 && J <= 16) ? 3 : 1) k_fiber_v(PassArgs a, FiberCoords fc,
                                                          int64_t nfibers, float *V) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
@@ -183,30 +184,61 @@ __global__ void __launch_bounds__(kFibThreads) k_fiber_v(PassArgs a, FiberCoords
         for (int q = 0; q < JL; ++q) vq[q] = vp[q];
         if (ok) store_run<JL>(V + f * J + sub * JL, vq);
     };
-    fetch(first);
     if constexpr (PIPE) {
-        Rows<NO, CT> w;
-        bool ok;
-        {
-            int32_t ci[NO];
+        // two fibers per group and iteration (f and f + stride): every float4 of
+        // B read from shared memory serves both products
+        int32_t ncB[NO];
+        auto fetch2 = [&](int64_t f) {
+            fetch(f);
 #pragma unroll
-            for (int q = 0; q < NO; ++q) ci[q] = nc[q];
-            fetch(first + stride);
-            ok = fiber_rows<R, CT, NO>(a, ci, first < nfibers, sub, w);
-        }
-        for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
+            for (int q = 0; q < NO; ++q)
+                ncB[q] = (f + stride < nfibers && q < a.N - 1) ? __ldg(fc.c[q] + f + stride) : 0;
+        };
+        auto rows2 = [&](int64_t f, Rows<NO, CT> &wa, bool &oka, Rows<NO, CT> &wb, bool &okb) {
+            int32_t ca[NO], cb[NO];
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+                ca[q] = nc[q];
+                cb[q] = ncB[q];
+            }
+            fetch2(f + 2 * stride);
+            oka = fiber_rows<R, CT, NO>(a, ca, f < nfibers, sub, wa);
+            okb = fiber_rows<R, CT, NO>(a, cb, f + stride < nfibers, sub, wb);
+        };
+        fetch2(first);
+        Rows<NO, CT> wa, wb;
+        bool oka, okb;
+        rows2(first, wa, oka, wb, okb);
+        for (int64_t f0 = warp_first; f0 < nfibers; f0 += 2 * stride) {
             const int64_t f = f0 + lane / T;
-            int32_t ci[NO];
+            Rows<NO, CT> na, nb;
+            bool okna, oknb;
+            rows2(f + 2 * stride, na, okna, nb, oknb);
+            const float4 pa = product<NO, CT>(wa), pb = product<NO, CT>(wb);
+            float va[J], vb[J];
 #pragma unroll
-            for (int q = 0; q < NO; ++q) ci[q] = nc[q];
-            fetch(f + 2 * stride);
-            Rows<NO, CT> wn;
-            const bool okn = fiber_rows<R, CT, NO>(a, ci, f + stride < nfibers, sub, wn);
-            emit(f, ok, w);
-            w = wn;
-            ok = okn;
+            for (int j = 0; j < J; ++j) {
+                const float4 b = *reinterpret_cast<const float4 *>(&sB[j * R + 4 * sub]);
+                va[j] = fmaf(b.x, pa.x, fmaf(b.y, pa.y, fmaf(b.z, pa.z, b.w * pa.w)));
+                vb[j] = fmaf(b.x, pb.x, fmaf(b.y, pb.y, fmaf(b.z, pb.z, b.w * pb.w)));
+            }
+            group_reduce_scatter<T, J>(va, sub);
+            group_reduce_scatter<T, J>(vb, sub);
+            float qa[JL], qb[JL];
+#pragma unroll
+            for (int q = 0; q < JL; ++q) {
+                qa[q] = va[q];
+                qb[q] = vb[q];
+            }
+            if (oka) store_run<JL>(V + f * J + sub * JL, qa);
+            if (okb) store_run<JL>(V + (f + stride) * J + sub * JL, qb);
+            wa = na;
+            wb = nb;
+            oka = okna;
+            okb = oknb;
         }
     } else {
+        fetch(first);
         for (int64_t f0 = warp_first; f0 < nfibers; f0 += stride) {
             const int64_t f = f0 + lane / T;
             int32_t ci[NO];
