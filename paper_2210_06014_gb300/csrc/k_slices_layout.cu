@@ -213,13 +213,14 @@ __device__ __forceinline__ bool long_piece(const SliceArgs &g, int64_t t, int si
 
 constexpr int kComposeGroups = 8;  // lane groups per block of k_slices_compose
 
-// X (the running block map, rows of X.M then X.c) lives in shared memory; lane
+// Form for J = 32 or lanes holding more than 4 rows (J/T > 4).  X (the running block map,
+// rows of X.M then X.c) lives in shared memory; lane
 // `sub` owns columns [sub*JL, (sub+1)*JL) of X.M and rows [sub*JL, ...) of X.c.
 // Each product X <- X o P first pulls the lane's column slice of P.M and all of
 // P.c into registers (one memory latency per product), then computes the new
 // columns from the whole of X; a group barrier separates reads from writes.
 template <int R, int J>
-__global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(SliceArgs g) {
+__global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose_smem(SliceArgs g) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
     constexpr int MS = J * J + J;
@@ -294,6 +295,109 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
 #pragma unroll
             for (int q = 0; q < JL; ++q) out[J * J + sub * JL + q] = X[J * J + sub * JL + q];
             __syncwarp(m);
+        }
+    }
+}
+
+// Form for J <= 16 and J/T <= 4.  X (the running block map) lives in registers: lane `sub` holds rows
+// [sub*JL, (sub+1)*JL) of X.M and of X.c.  The group stages each piece map P in
+// shared memory with cp.async, two buffers deep (the next P is in flight while
+// the current product runs); every lane reads P whole (broadcast) and forms its
+// rows of X o P:  X.M <- X.M P.M,  X.c <- X.M P.c + X.c, each entry summed
+// over l in ascending order.
+template <int R, int J>
+__global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(SliceArgs g) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int MS = J * J + J;
+    constexpr int CH = MS / 4;  // 16-byte chunks of one map
+    __shared__ __align__(16) float sP[kComposeGroups * 2 * MS];
+    const int sub = threadIdx.x & (T - 1);
+    const int gid = threadIdx.x / T;
+    const unsigned m = group_mask<T>(threadIdx.x & 31);
+    float *buf = sP + gid * 2 * MS;
+    auto stage = [&](const float *P, float *dst) {
+        for (int c = sub; c < CH; c += T) {
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 4 * c));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(P + 4 * c)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int64_t groups = (int64_t)gridDim.x * kComposeGroups;
+    for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
+        for (int side = 0; side < 2; ++side) {
+            int32_t r;
+            int64_t s, e;
+            if (!long_piece(g, t, side, r, s, e)) continue;
+            const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
+            const int64_t Bc = block_len(t1 - t0 + 1);
+            if ((t - t0) % Bc != 0) continue;
+            const int64_t tl = min(t + Bc - 1, t1);
+            if (tl == t) continue;  // a block of one piece is already its own map
+            auto map_of = [&](int64_t u) {
+                return g.maps + (u * 2 + piece_slot(s, u, g.W)) * (int64_t)MS;
+            };
+            stage(map_of(tl - 1), buf);
+            float X[JL][J], Xc[JL];
+            {
+                const float *P = map_of(tl);
+#pragma unroll
+                for (int q = 0; q < JL; ++q) {
+#pragma unroll
+                    for (int k = 0; k < J; k += 4) {
+                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(
+                            P + (sub * JL + q) * J + k));
+                        X[q][k] = v.x; X[q][k + 1] = v.y; X[q][k + 2] = v.z; X[q][k + 3] = v.w;
+                    }
+                    Xc[q] = __ldcg(P + J * J + sub * JL + q);
+                }
+            }
+            int cur = 0;
+            for (int64_t u = tl - 1; u >= t; --u) {
+                if (u > t) {
+                    stage(map_of(u - 1), buf + (cur ^ 1) * MS);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                }
+                __syncwarp(m);  // every lane's chunks of P have landed
+                const float *P = buf + cur * MS;
+#pragma unroll
+                for (int q = 0; q < JL; ++q) {
+                    float nrow[J];
+#pragma unroll
+                    for (int k = 0; k < J; ++k) nrow[k] = 0.f;
+                    float acc = Xc[q];
+#pragma unroll
+                    for (int l = 0; l < J; ++l) {
+                        const float x = X[q][l];
+#pragma unroll
+                        for (int k = 0; k < J; k += 4) {
+                            const float4 pv = *reinterpret_cast<const float4 *>(P + l * J + k);
+                            nrow[k] = fmaf(x, pv.x, nrow[k]);
+                            nrow[k + 1] = fmaf(x, pv.y, nrow[k + 1]);
+                            nrow[k + 2] = fmaf(x, pv.z, nrow[k + 2]);
+                            nrow[k + 3] = fmaf(x, pv.w, nrow[k + 3]);
+                        }
+                        acc = fmaf(x, P[J * J + l], acc);
+                    }
+#pragma unroll
+                    for (int k = 0; k < J; ++k) X[q][k] = nrow[k];
+                    Xc[q] = acc;
+                }
+                __syncwarp(m);  // P fully read before its buffer is refilled
+                cur ^= 1;
+            }
+            float *out = map_of(t);
+#pragma unroll
+            for (int q = 0; q < JL; ++q) {
+#pragma unroll
+                for (int k = 0; k < J; k += 4)
+                    *reinterpret_cast<float4 *>(out + (sub * JL + q) * J + k) =
+                        make_float4(X[q][k], X[q][k + 1], X[q][k + 2], X[q][k + 3]);
+                out[J * J + sub * JL + q] = Xc[q];
+            }
         }
     }
 }
@@ -459,8 +563,14 @@ cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t 
         constexpr int R_ = decltype(r_c)::value, J_ = decltype(j_c)::value;
         const int gpb = kSliceThreads / (R_ / 4);
         const int cth = kComposeGroups * (R_ / 4);
-        const int gc = grid_for(k_slices_compose<R_, J_>, cth, 0, kComposeGroups, g.ntiles, sms);
-        k_slices_compose<R_, J_><<<gc, cth, 0, st>>>(g);
+        if constexpr (J_ <= 16 && J_ / (R_ / 4) <= 4) {
+            const int gc = grid_for(k_slices_compose<R_, J_>, cth, 0, kComposeGroups, g.ntiles, sms);
+            k_slices_compose<R_, J_><<<gc, cth, 0, st>>>(g);
+        } else {
+            const int gc = grid_for(k_slices_compose_smem<R_, J_>, cth, 0, kComposeGroups, g.ntiles,
+                                    sms);
+            k_slices_compose_smem<R_, J_><<<gc, cth, 0, st>>>(g);
+        }
         const int gb = grid_for(k_slices_combine<R_, J_>, kSliceThreads, 0, gpb, g.ntiles, sms);
         k_slices_combine<R_, J_><<<gb, kSliceThreads, 0, st>>>(g);
     });

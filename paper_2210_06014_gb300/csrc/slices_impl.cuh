@@ -551,14 +551,14 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     const PassArgs &a = g.a;
     // The map is kept as M = alpha^n M', c = alpha^n c' (n = steps since the
     // last fold), so one step is a pure rank-1 FFMA update:
-    //   M' <- M' - (lr/alpha) v (v^T M'),
-    //   c' <- c' - (lr/alpha) v (v^T c') + lr x alpha^-(n+1) v;
-    // the factor alpha^n is folded back in every 16 steps and at the end.
+    //   M' <- M' + v (nvc w),  w = v^T M',  nvc = -lr/alpha,
+    //   c' <- c' + v (nvc s) + lr x alpha^-(n+1) v,  s = v . c';
+    // the factor alpha^n is folded back in at the end, and earlier only if it
+    // falls below 2^-20 (large lr * lambda), so alpha^-(n+1) stays bounded.
     const float alpha = 1.f - a.lr * a.lam;
     const float ainv = 1.f / alpha;
     const float nvc = -a.lr * ainv;
     float apow = 1.f, pw = ainv;
-    int since = 0;
     float M[J][JC], cv[JL];
 #pragma unroll
     for (int q = 0; q < J; ++q) {
@@ -577,7 +577,6 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         for (int q = 0; q < JL; ++q) cv[q] *= apow;
         apow = 1.f;
         pw = ainv;
-        since = 0;
     };
     auto apply = [&](const float (&v)[J], const float (&vl)[JL], float x, bool ok) {
         // w = v^T M' on the lane's columns (two partial sums each)
@@ -598,17 +597,19 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         sc = group_sum_m<T>(sc, m);
         if (ok) {
             const float xs = a.lr * x * pw;
+            const float ns = nvc * sc;
+#pragma unroll
+            for (int k = 0; k < JC; ++k) w[k] *= nvc;
 #pragma unroll
             for (int q = 0; q < J; ++q) {
-                const float nv = nvc * v[q];
 #pragma unroll
-                for (int k = 0; k < JC; ++k) M[q][k] = fmaf(nv, w[k], M[q][k]);
+                for (int k = 0; k < JC; ++k) M[q][k] = fmaf(v[q], w[k], M[q][k]);
             }
 #pragma unroll
-            for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vl[q], fmaf(nvc * vl[q], sc, cv[q]));
+            for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vl[q], fmaf(vl[q], ns, cv[q]));
             apow *= alpha;
             pw *= ainv;
-            if (++since == 16) fold();
+            if (apow < 0x1p-20f) fold();
         }
     };
     if constexpr (FV && MapRing<R, J>::use) {
