@@ -776,14 +776,19 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "ready": None}
 
     def step(timed: bool, inp=resident):
-        """One epoch over the inputs `inp`.  inp["ready"]: None, or one event per
-        mode and one for the test set, recorded after that input's host-to-device
-        copy; the step waits on each before it first reads that input."""
+        """One epoch over the inputs `inp`.  inp["ready"]: None, or per mode and
+        for the test set a list of events recorded after that input's
+        host-to-device copies; the step waits on them before it first reads
+        that input."""
         ready = inp["ready"]
         sls = inp["slices"]
-        for n in range(N):
+        def wait_ready(i):
             if ready is not None:
-                stream.wait_event(ready[n])
+                for e in ready[i]:
+                    stream.wait_event(e)
+
+        for n in range(N):
+            wait_ready(n)
             if timed:
                 a, b = ev_pair("factor")
                 a.record(stream)
@@ -814,8 +819,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             dec.refresh(n)
             if timed:
                 b.record(stream)
-        if ready is not None:
-            stream.wait_event(ready[N])
+        wait_ready(N)
         if timed:
             a, b = ev_pair("loss")
             a.record(stream)
@@ -931,24 +935,31 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         host = [[t.cpu().pin_memory() for t in g] for g in groups_of(sets[0])]
         h2d = sum(t.numel() * t.element_size() for g in host for t in g)
         hloss = torch.zeros(2, dtype=torch.float64).pin_memory()
-        copy_stream = torch.cuda.Stream()
+        # two copy streams take the tensors of each group in turn (more than
+        # one copy engine); a group is ready when both streams have passed it
+        copy_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         done = [torch.cuda.Event(), torch.cuda.Event()]
 
         def enqueue_copies(k):
             inp = sets[k % 2]
             ready = []
-            copy_stream.wait_event(done[k % 2])  # the step that last read this set
-            with torch.cuda.stream(copy_stream):
-                for g_dev, g_host in zip(groups_of(inp), host):
-                    for d, h in zip(g_dev, g_host):
+            for cs in copy_streams:
+                cs.wait_event(done[k % 2])  # the step that last read this set
+            for g_dev, g_host in zip(groups_of(inp), host):
+                for j, (d, h) in enumerate(zip(g_dev, g_host)):
+                    with torch.cuda.stream(copy_streams[j % 2]):
                         d.copy_(h, non_blocking=True)
+                evs = []
+                for cs in copy_streams:
                     e = torch.cuda.Event()
-                    e.record(copy_stream)
-                    ready.append(e)
+                    e.record(cs)
+                    evs.append(e)
+                ready.append(evs)
             inp["ready"] = ready
 
         def e2e_steps(nsteps):
-            copy_stream.wait_stream(stream)
+            for cs in copy_streams:
+                cs.wait_stream(stream)
             enqueue_copies(0)
             for k in range(nsteps):
                 if k + 1 < nsteps:
