@@ -79,25 +79,38 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(PassArgs a, double *__res
     const int64_t p0 = (int64_t)blockIdx.x * span;
     const int64_t p1 = min(a.count, p0 + span);
     double s2 = 0.0, s1 = 0.0;
-    for (int64_t t0 = p0 + (int64_t)warp * GPW; t0 < p1; t0 += (int64_t)WARPS * GPW) {
-        const int64_t pos = t0 + gw;
-        bool ok = pos < p1;
+    // the coordinates and value of the group's next nonzero are loaded one
+    // iteration ahead, so the row gathers of a nonzero never wait on them
+    struct Next {
+        int32_t ik[kMaxOrder];
+        float x;
+        bool ok;
+    };
+    auto fetch = [&](int64_t pos, Next &nx) {
+        nx.ok = pos < p1;
         int64_t s = 0;
-        if (ok) ok = sample_at(a, a.base + pos, s);
+        if (nx.ok) nx.ok = sample_at(a, a.base + pos, s);
+#pragma unroll
+        for (int k = 0; k < kMaxOrder; ++k) nx.ik[k] = (nx.ok && k < a.N) ? __ldg(a.idx[k] + s) : 0;
+        nx.x = nx.ok ? __ldg(a.val + s) : 0.f;
+    };
+    Next cur;
+    fetch(p0 + (int64_t)warp * GPW + gw, cur);
+    for (int64_t t0 = p0 + (int64_t)warp * GPW; t0 < p1; t0 += (int64_t)WARPS * GPW) {
+        Next nx;
+        fetch(t0 + (int64_t)WARPS * GPW + gw, nx);
+        bool ok = cur.ok;
         int32_t ik[kMaxOrder];
 #pragma unroll
         for (int k = 0; k < kMaxOrder; ++k) {
-            ik[k] = 0;
-            if (ok && k < a.N) {
-                ik[k] = __ldg(a.idx[k] + s);
-                if ((uint32_t)ik[k] >= (uint32_t)a.dims[k]) {
-                    atomicOr(a.err, kErrIndex);
-                    ok = false;
-                }
+            ik[k] = cur.ik[k];
+            if (ok && k < a.N && (uint32_t)ik[k] >= (uint32_t)a.dims[k]) {
+                atomicOr(a.err, kErrIndex);
+                ok = false;
             }
         }
         float4 p = make_float4(ok ? 1.f : 0.f, ok ? 1.f : 0.f, ok ? 1.f : 0.f, ok ? 1.f : 0.f);
-        const float x = ok ? __ldg(a.val + s) : 0.f;
+        const float x = ok ? cur.x : 0.f;
 #pragma unroll
         for (int k0 = 0; k0 < kMaxOrder; k0 += 4) {
             if (k0 < a.N) {
@@ -112,6 +125,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(PassArgs a, double *__res
                 for (int u = 0; u < 4; ++u) mul4(p, c[u]);
             }
         }
+        cur = nx;
         const float xh = group_sum<T>((p.x + p.y) + (p.z + p.w));
         if (ok && sub == 0) {
             const double e = (double)x - (double)xh;
