@@ -244,8 +244,17 @@ sft_status sft_init(const sft_config *cfg, float *const *A, float *const *B, voi
     // auxiliary streams for the concurrent kernels of a slice factor pass; if
     // they cannot be created everything runs on the caller's stream
     bool aux_ok = true;
-    for (int i = 0; i < 2 && aux_ok; ++i)
-        aux_ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess;
+    // aux[0]: chains; aux[1]: maps, the longest of the three kernels, at the
+    // highest stream priority so that its blocks are scheduled first
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        prio_greatest = prio_least = 0;
+    }
+    aux_ok = cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking) == cudaSuccess;
+    if (aux_ok)
+        aux_ok = cudaStreamCreateWithPriority(&c->aux[1], cudaStreamNonBlocking, prio_greatest) ==
+                 cudaSuccess;
     for (int i = 0; i < 3 && aux_ok; ++i)
         aux_ok = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!aux_ok) {

@@ -807,6 +807,13 @@ template <bool FV, int NB, int R, int J, typename CT>
 void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
+    // maps first: it is the longest of the three, so its blocks take the SMs first
+    if (with_maps && g.ntiles > 1) {
+        const int gm = grid_for(k_slices_maps<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles,
+                                sms);
+        k_slices_maps<FV, NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
+        *launches += 1;
+    }
     if (g.ntiles > 1) {
         // the list holds at most one slice per tile boundary
         const int gch = grid_for(k_slices_chains<FV, NB, R, J, CT>, kSliceThreads, 0, gpb,
@@ -817,12 +824,6 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
     const int gd = grid_for(k_slices_tiles<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
     k_slices_tiles<FV, NB, R, J, CT><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
     *launches += 1;
-    if (with_maps && g.ntiles > 1) {
-        const int gm = grid_for(k_slices_maps<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles,
-                                sms);
-        k_slices_maps<FV, NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
-        *launches += 1;
-    }
 }
 
 template <bool FV, int NB, int R, int J, typename CT>
