@@ -121,7 +121,8 @@ sft_status sft_update_factors(sft_ctx *ctx, int32_t mode, const int32_t *const *
  * B^(mode) as it stood at its start: G = sum_s e_s a_{i_mode(s)} p_s^T and
  * B^(mode) += lr * (G / M_b - lambda B^(mode)).  batch = nnz gives the single
  * update per pass of Algorithm 5.  Sums are in a fixed order in both modes.
- * batch must be <= max_batch or equal to nnz. */
+ * batch must be <= max_batch or equal to nnz.  With SFT_BF16 and R in {16, 32}
+ * the contraction G runs on the tensor cores (sft_set_tensor_cores). */
 sft_status sft_update_core(sft_ctx *ctx, int32_t mode, const int32_t *const *idx,
                            const float *val, const uint32_t *perm, int64_t nnz, int64_t batch,
                            float lr, float lambda);
