@@ -483,6 +483,10 @@ static int64_t slice_W(const sft_ctx *c, int64_t nnz) {
     return c->slice_tile > 0 ? c->slice_tile : slice_tile_length(nnz, c->sms);
 }
 
+static int64_t slice_core_W(const sft_ctx *c, int64_t nnz) {
+    return c->slice_tile > 0 ? c->slice_tile : slice_core_tile_length(nnz, c->sms);
+}
+
 // Longest crossing slice run as one element-by-element chain.  A chain step
 // is a dependent sequence of shuffles and FMAs (a few hundred cycles), so
 // chains much longer than a couple of tiles become the pass's tail; measured
@@ -573,7 +577,7 @@ sft_status sft_update_core_slices(sft_ctx *c, int32_t mode, const int32_t *const
     for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
         a.base = b0;
         a.count = nnz - b0 < batch ? nnz - b0 : batch;
-        cudaError_t e = launch_core_slices(a, row_ptr, slice_W(c, a.count), c->J[mode], c->R,
+        cudaError_t e = launch_core_slices(a, row_ptr, slice_core_W(c, a.count), c->J[mode], c->R,
                                            c->core_partials, c->core_max_blocks, c->stream, c->sms,
                                            &c->launches);
         if (e != cudaSuccess) return cuda_fail(c, e, "slice core launch");
@@ -664,7 +668,7 @@ sft_status sft_update_core_fibers(sft_ctx *c, int32_t mode, const int32_t *const
     for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
         a.base = b0;
         a.count = nnz - b0 < batch ? nnz - b0 : batch;
-        cudaError_t e = launch_core_fibers(a, row_ptr, slice_W(c, a.count), fid, fcoord, nfibers, P,
+        cudaError_t e = launch_core_fibers(a, row_ptr, slice_core_W(c, a.count), fid, fcoord, nfibers, P,
                                            c->J[mode], c->R, c->core_partials, c->core_max_blocks,
                                            c->stream, c->sms, &c->launches, b0 == 0);
         if (e != cudaSuccess) return cuda_fail(c, e, "fiber core launch");

@@ -82,6 +82,7 @@ struct SliceStreams {
 int64_t slice_sort_length(int64_t nnz);
 size_t slice_maps_bytes(int64_t ntiles, int J);
 int slice_tile_length(int64_t nnz, int sms);
+int slice_core_tile_length(int64_t nnz, int sms);
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches);
