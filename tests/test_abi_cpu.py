@@ -25,7 +25,7 @@ def lib():
     return sft.load()
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_core_calls():
     names = declared_entry_points()
     for must in ["sft_init", "sft_refresh_C", "sft_update_factors", "sft_update_core", "sft_loss"]:
         assert must in names
