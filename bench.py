@@ -902,8 +902,9 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
 
         def groups_of(inp):
             if inp["slices"]:
+                # fiber coordinates: only the first nfibers entries are in use
                 gs = [sl.idx + [sl.val, sl.row_ptr]
-                      + ([sl.fid] + [c for c in sl.fcoord if c is not None]
+                      + ([sl.fid] + [c[:sl.nfibers] for c in sl.fcoord if c is not None]
                          if sl.fid is not None else [])
                       for sl in inp["slices"]]
             else:
