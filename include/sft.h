@@ -304,6 +304,18 @@ sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
  * next sft_sync / sft_loss. */
 sft_status sft_set_tensor_cores(sft_ctx *ctx, int32_t enable);
 
+/* Time limit, in nanoseconds, of the tensor-core kernels' waits on their own
+ * TMA copies and MMAs (mbarrier waits of the main loop; default 2 s, at most
+ * 60 s).  A wait that runs out makes the kernel flag it, stop, wait once more
+ * -- always with the full 2 s bound -- for the copies and MMAs it issued,
+ * free its tensor memory and return; the next sft_sync / sft_loss reports
+ * SFT_ETIMEOUT and the context stays usable.  The result of the call whose
+ * wait ran out is not valid: a refresh leaves C^(n) partly stale, a core pass
+ * moves B^(n) by a partial gradient (blocks whose wait ran out add nothing).  limit_ns = 0 gives up without waiting,
+ * so that the expiry path can be made to run on a normal launch (this is how
+ * it is tested).  Does not affect the float32 kernels. */
+sft_status sft_set_tc_wait_limit(sft_ctx *ctx, int64_t limit_ns);
+
 /* Per-mode autotuner of the slice factor pass: times the pass of `mode` with
  * several limits on the length of a crossing slice that is run whole as one
  * chain (2W, 1024 .. 16384, and every crossing slice; longer ones go through
@@ -333,8 +345,10 @@ sft_status sft_autotune_slices(sft_ctx *ctx, int32_t mode, const int32_t *const 
  * with deterministic = 1 (same kernels, same result), taking every operand
  * directly: the order, mode lengths dims[N], ranks J[N] and R; mode; the
  * device matrices A_mode (I_mode x J_mode, updated in place), B_mode
- * (J_mode x R) and C[N] (I_k x R, the cached products); the COO set idx[N],
- * val, optional perm, nnz; batch, lr, lambda; the cudaStream_t `stream`.
+ * (J_mode x R) and C[N] (I_k x R, the cached products, FLOAT32: the layout of
+ * an SFT_FP32 decomposition; bfloat16 products are not accepted here); the
+ * COO set idx[N], val, optional perm, nnz; batch, lr, lambda (finite); the
+ * cudaStream_t `stream`.
  * Its scratch (the per-chunk row sums of a minibatch and the bad-data flag) is
  * a fixed ~529 KB array of device memory inside the library image, kept by
  * every GPU that loads the library until the process exits; no call allocates,
@@ -342,13 +356,15 @@ sft_status sft_autotune_slices(sft_ctx *ctx, int32_t mode, const int32_t *const 
  *   - batch must be 1..4096 (the scratch holds one minibatch of at most 4096
  *     nonzeros); a larger batch returns SFT_ENOTSUP and does nothing;
  *   - the first call on a device looks up the array's device address (with that
- *     device current) and caches it; make that first call before any stream
- *     capture;
+ *     device current) and caches it;
+ *   - every call reads the bad-data flag back and waits for `stream` before it
+ *     returns, so it cannot be recorded into a CUDA graph: on a stream that is
+ *     being captured it returns SFT_ENOTSUP before enqueuing anything;
  *   - all calls share the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and must not be issued;
- *   - the call waits for `stream` and returns SFT_EINVAL if a kernel flagged
- *     bad data (coordinates out of range, permutation entries >= nnz), which
- *     was then skipped.
+ *   - SFT_EINVAL is returned after the wait if a kernel flagged bad data
+ *     (coordinates out of range, permutation entries >= nnz), which was then
+ *     skipped.
  * Returns SFT_EINVAL / SFT_ENOTSUP for bad or unsupported arguments before any
  * launch, SFT_ECUDA on a CUDA error. */
 sft_status sft_update_factors_noalloc(int32_t order, const int64_t *dims, const int32_t *J,

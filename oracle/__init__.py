@@ -68,6 +68,8 @@ def _load():
             lib.orc_factor_pass.restype = ctypes.c_int
             lib.orc_core_pass.argtypes = pass_args
             lib.orc_core_pass.restype = ctypes.c_int
+            lib.orc_factor_pass_scaled.argtypes = pass_args + [_dp]
+            lib.orc_factor_pass_scaled.restype = ctypes.c_int
             lib.orc_loss.argtypes = [ctypes.c_int, ctypes.c_int, _pp_d, _pp_i32, fp, i64, _dp, _dp]
             lib.orc_loss.restype = None
             lib.orc_loss_grad.argtypes = [ctypes.c_int, ip64, ip32, ctypes.c_int, _pp_d, _pp_d,
@@ -153,7 +155,7 @@ class Model:
                                    A, B, _ptr_array(idx, ctypes.c_int32), nnz, _ptr_d(out))
         return out
 
-    def _pass(self, fn, n, idx, val, perm, batch, lr, lam):
+    def _pass(self, fn, n, idx, val, perm, batch, lr, lam, *extra):
         idx, val = self._coo(idx, val)
         nnz = len(val)
         if perm is not None:
@@ -167,13 +169,26 @@ class Model:
         rc = fn(self.N, self.I.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                 J.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.R, int(n), A, B, C,
                 _ptr_array(idx, ctypes.c_int32), val.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                pptr, nnz, int(batch), float(lr), float(lam))
+                pptr, nnz, int(batch), float(lr), float(lam), *extra)
         if rc != 0:
             raise RuntimeError(f"oracle pass failed with code {rc}")
 
     def factor_pass(self, n, idx, val, perm=None, batch=1, lr=0.01, lam=0.01) -> None:
         """Update A[n] over every nonzero (Eq. (9)-(10)); C[n] is NOT refreshed."""
         self._pass(_load().orc_factor_pass, n, idx, val, perm, batch, lr, lam)
+
+    def factor_pass_scaled(self, n, idx, val, perm=None, batch=1, lr=0.01, lam=0.01):
+        """factor_pass, also returning the per-entry rounding scales (S1, S2) of
+        the pass (I_n x J_n each): S1 = sum over the row's samples of
+        lr ((|x| + |a|.|v|) |v|_j + lam |a_j|) with |v| built from |A| |B|, and
+        S2 = sum over the row's samples of |a_j| as each step read it.  They
+        bound the rounding of a float32 run of the same pass; A moves exactly
+        as in factor_pass."""
+        In, Jn = int(self.I[n]), int(self.J[n])
+        scale = np.zeros(2 * In * Jn, dtype=np.float64)
+        self._pass(_load().orc_factor_pass_scaled, n, idx, val, perm, batch, lr, lam,
+                   _ptr_d(scale))
+        return scale[:In * Jn].reshape(In, Jn), scale[In * Jn:].reshape(In, Jn)
 
     def core_pass(self, n, idx, val, perm=None, batch=1, lr=0.01, lam=0.01) -> None:
         """Update B[n] over every nonzero (Eq. (9), (11)); C[n] is NOT refreshed."""

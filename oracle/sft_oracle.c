@@ -141,6 +141,18 @@ static void core_times(int J, int R, const double *B, const double *p, double *v
     }
 }
 
+/* |c^(k)_i|_r bound: sum_j |A^(k)[i][j]| |B^(k)[j][r]| (the magnitude a float32
+ * refresh of that row rounds against), used only by the rounding scale below. */
+static void abs_cached_row(int J, int R, const double *A, const double *B, int64_t i, double *out)
+{
+    for (int r = 0; r < R; ++r) {
+        double acc = 0.0;
+        for (int j = 0; j < J; ++j)
+            acc += fabs(A[i * J + j]) * fabs(B[(int64_t)j * R + r]);
+        out[r] = acc;
+    }
+}
+
 /* One factor pass over mode n (Algorithm 2, factor module; Eq. (9)-(10)).
  * For each minibatch (consecutive slice of the permutation, the last one
  * shorter):
@@ -149,11 +161,19 @@ static void core_times(int J, int R, const double *B, const double *p, double *v
  *        and its term t_s = e_s v_s - lambda a_{i_n};
  *   (ii) the terms of each row are summed in sample order and the row moves by
  *        lr times that sum.
- * C^(n) itself is not read (it is stale while A^(n) moves). */
-int orc_factor_pass(int N, const int64_t *I, const int *J, int R, int n,
-                    double *const *A, const double *const *B, const double *const *C,
-                    const int32_t *const *idx, const float *val, const uint32_t *perm,
-                    int64_t nnz, int64_t batch, double lr, double lam)
+ * C^(n) itself is not read (it is stale while A^(n) moves).
+ *
+ * scale (optional, I_n x J_n, accumulated into) receives, per row and entry,
+ * the magnitudes that bound the rounding of a lower-precision run of the same
+ * pass: S1 = sum over the row's samples of lr ((|x| + |a|.|v|) |v|_j + lambda |a_j|)
+ * with |v| = |B^(n)| |p| and |p| = prod_{k != n} |A^(k)| |B^(k)| rows, and
+ * S2 = sum over the row's samples of |a_j| (the row as each step reads it).
+ * scale[0 .. I_n J_n) holds S1, scale[I_n J_n .. 2 I_n J_n) holds S2.  It
+ * does not change the pass. */
+static int factor_pass_impl(int N, const int64_t *I, const int *J, int R, int n,
+                            double *const *A, const double *const *B, const double *const *C,
+                            const int32_t *const *idx, const float *val, const uint32_t *perm,
+                            int64_t nnz, int64_t batch, double lr, double lam, double *scale)
 {
     if (N < 2 || N > ORC_MAX_ORDER || n < 0 || n >= N || batch < 1 || nnz < 0)
         return ORC_EINVAL;
@@ -163,14 +183,18 @@ int orc_factor_pass(int N, const int64_t *I, const int *J, int R, int n,
     const double *Bn = B[n];
     double *p = malloc(sizeof(double) * R);
     double *v = malloc(sizeof(double) * Jn);
+    double *pa = malloc(sizeof(double) * R);
+    double *ca = malloc(sizeof(double) * R);
+    double *va = malloc(sizeof(double) * Jn);
     int64_t cap = batch < nnz ? batch : (nnz > 0 ? nnz : 1);
     double *term = malloc(sizeof(double) * (size_t)cap * Jn);
     int64_t *row = malloc(sizeof(int64_t) * (size_t)cap);
     double *delta = malloc(sizeof(double) * (size_t)In * Jn);
     unsigned char *touched = calloc((size_t)In, 1);
     int64_t *order_touched = malloc(sizeof(int64_t) * (size_t)cap);
-    if (!p || !v || !term || !row || !delta || !touched || !order_touched) {
-        free(p); free(v); free(term); free(row); free(delta); free(touched); free(order_touched);
+    if (!p || !v || !pa || !ca || !va || !term || !row || !delta || !touched || !order_touched) {
+        free(p); free(v); free(pa); free(ca); free(va); free(term); free(row); free(delta);
+        free(touched); free(order_touched);
         return ORC_ENOMEM;
     }
     for (int64_t b0 = 0; b0 < nnz; b0 += batch) {
@@ -188,6 +212,31 @@ int orc_factor_pass(int N, const int64_t *I, const int *J, int R, int n,
             for (int j = 0; j < Jn; ++j)
                 term[t * Jn + j] = e * v[j] - lam * An[i * Jn + j];
             row[t] = i;
+            if (scale) {
+                for (int r = 0; r < R; ++r)
+                    pa[r] = 1.0;
+                for (int k = 0; k < N; ++k) {
+                    if (k == n)
+                        continue;
+                    abs_cached_row(J[k], R, A[k], B[k], idx[k][s], ca);
+                    for (int r = 0; r < R; ++r)
+                        pa[r] *= ca[r];
+                }
+                double xa = 0.0;
+                for (int j = 0; j < Jn; ++j) {
+                    double acc = 0.0;
+                    for (int r = 0; r < R; ++r)
+                        acc += fabs(Bn[(int64_t)j * R + r]) * pa[r];
+                    va[j] = acc;
+                    xa += fabs(An[i * Jn + j]) * acc;
+                }
+                const double ea = fabs((double)val[s]) + xa;
+                for (int j = 0; j < Jn; ++j) {
+                    const double aj = fabs(An[i * Jn + j]);
+                    scale[i * Jn + j] += lr * (ea * va[j] + lam * aj);
+                    scale[In * Jn + i * Jn + j] += aj;
+                }
+            }
         }
         /* (ii) per-row sums in sample order, then one move per touched row */
         int64_t ntouched = 0;
@@ -209,8 +258,29 @@ int orc_factor_pass(int N, const int64_t *I, const int *J, int R, int n,
             touched[i] = 0;
         }
     }
-    free(p); free(v); free(term); free(row); free(delta); free(touched); free(order_touched);
+    free(p); free(v); free(pa); free(ca); free(va); free(term); free(row); free(delta);
+    free(touched); free(order_touched);
     return ORC_OK;
+}
+
+int orc_factor_pass(int N, const int64_t *I, const int *J, int R, int n,
+                    double *const *A, const double *const *B, const double *const *C,
+                    const int32_t *const *idx, const float *val, const uint32_t *perm,
+                    int64_t nnz, int64_t batch, double lr, double lam)
+{
+    return factor_pass_impl(N, I, J, R, n, A, B, C, idx, val, perm, nnz, batch, lr, lam, NULL);
+}
+
+/* orc_factor_pass plus the rounding scale described above (scale: 2 I_n J_n
+ * doubles, zeroed by the caller). */
+int orc_factor_pass_scaled(int N, const int64_t *I, const int *J, int R, int n,
+                           double *const *A, const double *const *B, const double *const *C,
+                           const int32_t *const *idx, const float *val, const uint32_t *perm,
+                           int64_t nnz, int64_t batch, double lr, double lam, double *scale)
+{
+    if (!scale)
+        return ORC_EINVAL;
+    return factor_pass_impl(N, I, J, R, n, A, B, C, idx, val, perm, nnz, batch, lr, lam, scale);
 }
 
 /* One core pass over mode n (Algorithm 2, core module; Eq. (9), (11)).
@@ -292,8 +362,17 @@ double orc_loss_grad(int N, const int64_t *I, const int *J, int R, const double 
         memset(gA[n], 0, sizeof(double) * (size_t)I[n] * J[n]);
         memset(gB[n], 0, sizeof(double) * (size_t)J[n] * R);
     }
+    int Jmax = 1;
+    for (int n = 0; n < N; ++n)
+        if (J[n] > Jmax)
+            Jmax = J[n];
     double *p = malloc(sizeof(double) * R);
-    double *v = malloc(sizeof(double) * 64);
+    double *v = malloc(sizeof(double) * Jmax);
+    if (!p || !v) {
+        free(p);
+        free(v);
+        return NAN;
+    }
     double loss = 0.0;
     for (int64_t s = 0; s < nnz; ++s) {
         const double e = (double)val[s] - predict_cached(N, R, C, idx, s);

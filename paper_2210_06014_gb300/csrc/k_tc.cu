@@ -29,7 +29,7 @@
 namespace sft {
 namespace tc {
 
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: the default limit and the drain bound
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -85,13 +85,17 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
 }
 
 // Waits until the phase of parity `parity` of barrier b has completed, for at
-// most kWaitNs; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+// most limit_ns; false if the limit ran out.  A limit of 0 gives up without
+// looking (the wait has no time at all), which lets a caller make the expiry
+// path run on a normal launch.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity,
+                                          uint64_t limit_ns = kWaitNs) {
+    if (limit_ns == 0) return false;
     if (mbar_test(b, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_test(b, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
         __nanosleep(100);
     }
 }
@@ -200,7 +204,8 @@ template <int R, int J>
 __global__ void __launch_bounds__(kTcRefreshThreads) k_refresh_tc(const __grid_constant__ CUtensorMap mapA,
                                                                   const float *__restrict__ B,
                                                                   __nv_bfloat16 *__restrict__ C,
-                                                                  int64_t I, int *err) {
+                                                                  int64_t I, int *err,
+                                                                  uint64_t wait_ns) {
     static_assert(R == 16 || R == 32, "N = R must be a multiple of 16 for M = 128");
     static_assert(J % 8 == 0, "K = J must be a multiple of 8 for kind::tf32");
     constexpr uint32_t kTileBytes = 128u * J * 4u;
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(kTcRefreshThreads) k_refresh_tc(const __grid_c
                 tc::tma_load_2d(sA + q * 128 * 4, &mapA, 4 * q, (int32_t)(t * 128), &bar_tma);
         }
         tma_pending = true;
-        ok = __syncthreads_and(tc::mbar_wait(&bar_tma, phase));
+        ok = __syncthreads_and(tc::mbar_wait(&bar_tma, phase, wait_ns));
         if (!ok) break;
         tma_pending = false;
         if (threadIdx.x == 0) {
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kTcRefreshThreads) k_refresh_tc(const __grid_c
             tc::mma_commit(&bar_mma);
         }
         mma_pending = true;
-        ok = __syncthreads_and(tc::mbar_wait(&bar_mma, phase));
+        ok = __syncthreads_and(tc::mbar_wait(&bar_mma, phase, wait_ns));
         if (!ok) break;
         mma_pending = false;
         tc::fence_after_sync();
@@ -281,7 +286,8 @@ __global__ void __launch_bounds__(kTcRefreshThreads) k_refresh_tc(const __grid_c
     }
     if (!ok && threadIdx.x == 0) {
         atomicOr(err, kErrWait);
-        // one more bounded wait for the copies / MMAs this block issued
+        // one more wait, with the full bound, for the copies / MMAs this block
+        // issued, so that shared and tensor memory are released only after them
         if (tma_pending) tc::mbar_wait(&bar_tma, phase);
         if (mma_pending) tc::mbar_wait(&bar_mma, phase);
     }
@@ -320,7 +326,7 @@ bool refresh_tc_supported(int J, int R) {
 }
 
 cudaError_t launch_refresh_tc(const float *A, const float *B, void *C, int64_t I, int J, int R,
-                              int *err, cudaStream_t st, int sms) {
+                              int *err, uint64_t wait_ns, cudaStream_t st, int sms) {
     if (!refresh_tc_supported(J, R) || I < 1) return cudaErrorInvalidValue;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
@@ -338,12 +344,12 @@ cudaError_t launch_refresh_tc(const float *A, const float *B, void *C, int64_t I
     int64_t blocks = ntiles < (int64_t)sms * 4 ? ntiles : (int64_t)sms * 4;
     auto *Cb = reinterpret_cast<__nv_bfloat16 *>(C);
     switch (R * 100 + J) {
-        case 1608: k_refresh_tc<16, 8><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
-        case 1616: k_refresh_tc<16, 16><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
-        case 1632: k_refresh_tc<16, 32><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
-        case 3208: k_refresh_tc<32, 8><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
-        case 3216: k_refresh_tc<32, 16><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
-        case 3232: k_refresh_tc<32, 32><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err); break;
+        case 1608: k_refresh_tc<16, 8><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
+        case 1616: k_refresh_tc<16, 16><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
+        case 1632: k_refresh_tc<16, 32><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
+        case 3208: k_refresh_tc<32, 8><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
+        case 3216: k_refresh_tc<32, 16><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
+        case 3232: k_refresh_tc<32, 32><<<(int)blocks, kTcRefreshThreads, 0, st>>>(map, B, Cb, I, err, wait_ns); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -369,7 +375,8 @@ constexpr int kTcCoreSmem = 2 * kTcBufBytes + 1024;  // two buffers + alignment 
 
 template <int R, int J, typename CT>
 __global__ void __launch_bounds__(kTcCoreThreads) k_core_grad_tc(PassArgs a,
-                                                                 float *__restrict__ partials) {
+                                                                 float *__restrict__ partials,
+                                                                 uint64_t wait_ns) {
     static_assert(R == 16 || R == 32, "N = R must be a multiple of 16 for M = 128");
     constexpr int T = R / 4;
     constexpr int JL = J / T;
@@ -411,7 +418,8 @@ __global__ void __launch_bounds__(kTcCoreThreads) k_core_grad_tc(PassArgs a,
     for (; c < nbatch; ++c) {
         const int buf = (int)(c & 1);
         if (c >= 2) {  // the MMAs of batch c - 2 have finished reading this buffer
-            ok = __syncthreads_and(tc::mbar_wait(&bar_mma[buf], (uint32_t)(((c - 2) >> 1) & 1)));
+            ok = __syncthreads_and(
+                tc::mbar_wait(&bar_mma[buf], (uint32_t)(((c - 2) >> 1) & 1), wait_ns));
             if (!ok) break;
         }
         uint8_t *tA = smem + buf * kTcBufBytes;
@@ -503,25 +511,33 @@ __global__ void __launch_bounds__(kTcCoreThreads) k_core_grad_tc(PassArgs a,
     // the last commit completes once every MMA of the block has
     const int64_t last = c - 1;
     if (ok && last >= 0)
-        ok = __syncthreads_and(tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1)));
+        ok = __syncthreads_and(
+            tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1), wait_ns));
+    if (!ok) {
+        // a wait ran out: flag it, then wait once more, with the full bound, for
+        // the MMAs this block issued before anything reads or frees tensor memory
+        if (threadIdx.x == 0) {
+            atomicOr(a.err, kErrWait);
+            if (last >= 0) tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1));
+        }
+        __syncthreads();
+    }
     tc::fence_after_sync();
     if (warp == 0) {
-        // accumulator rows j < J_n <= 32 live in tensor-memory lanes 0..31
+        // accumulator rows j < J_n <= 32 live in tensor-memory lanes 0..31; a
+        // block whose wait ran out contributes zeros
 #pragma unroll
         for (int h = 0; h < R / 16; ++h) {
             float g[16];
-            tc::tmem_ld16(tmem + 16u * h, g);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) g[q] = 0.f;
+            if (ok && last >= 0) tc::tmem_ld16(tmem + 16u * h, g);
             if (lane < J) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    partials[(int64_t)blockIdx.x * JR + lane * R + 16 * h + q] =
-                        (ok && last >= 0) ? g[q] : 0.f;
+                    partials[(int64_t)blockIdx.x * JR + lane * R + 16 * h + q] = g[q];
             }
         }
-    }
-    if (!ok && threadIdx.x == 0) {
-        atomicOr(a.err, kErrWait);
-        if (last >= 0) tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1));
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -534,12 +550,12 @@ __global__ void __launch_bounds__(kTcCoreThreads) k_core_grad_tc(PassArgs a,
 bool core_tc_supported(int J, int R) { return (R == 16 || R == 32) && 4 * J >= R; }
 
 cudaError_t launch_core_tc(const PassArgs &a, int J, int R, float *partials, int nblk,
-                           cudaStream_t st) {
+                           uint64_t wait_ns, cudaStream_t st) {
     if (!core_tc_supported(J, R)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcCoreSmem);
-        if (e == cudaSuccess) kernel<<<nblk, kTcCoreThreads, kTcCoreSmem, st>>>(a, partials);
+        if (e == cudaSuccess) kernel<<<nblk, kTcCoreThreads, kTcCoreSmem, st>>>(a, partials, wait_ns);
     };
     switch (R * 100 + J) {
         case 1604: go(k_core_grad_tc<16, 4, __nv_bfloat16>); break;

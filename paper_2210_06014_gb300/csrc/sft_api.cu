@@ -43,6 +43,7 @@ struct sft_ctx {
     int64_t slice_max_direct = 0;  // 0 = automatic
     int64_t slice_lseq_mode[kMaxOrder] = {};  // per-mode choice of sft_autotune_slices (0 = none)
     int tensor_cores = 1;  // tcgen05 refresh / core gradient for bfloat16 cached products
+    uint64_t tc_wait_ns = 2000000000ull;  // limit of the tensor-core kernels' waits
     std::string last_error;
 };
 
@@ -276,7 +277,7 @@ sft_status sft_refresh_C(sft_ctx *c, int32_t mode) {
         cudaError_t e;
         if (c->cbf16 && c->tensor_cores && refresh_tc_supported(c->J[n], c->R))
             e = launch_refresh_tc(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R, c->err,
-                                  c->stream, c->sms);
+                                  c->tc_wait_ns, c->stream, c->sms);
         else
             e = launch_refresh(c->A[n], c->B[n], c->C[n], c->dims[n], c->J[n], c->R,
                                c->cbf16 != 0, c->stream, c->sms);
@@ -333,7 +334,8 @@ sft_status sft_update_core(sft_ctx *c, int32_t mode, const int32_t *const *idx, 
         int nblk = core_blocks_for(a.count, c->sms);
         if (nblk > c->core_max_blocks) nblk = c->core_max_blocks;
         const bool tc = c->cbf16 && c->tensor_cores && core_tc_supported(c->J[mode], c->R);
-        cudaError_t e = tc ? launch_core_tc(a, c->J[mode], c->R, c->core_partials, nblk, c->stream)
+        cudaError_t e = tc ? launch_core_tc(a, c->J[mode], c->R, c->core_partials, nblk,
+                                            c->tc_wait_ns, c->stream)
                            : launch_core(a, c->J[mode], c->R, c->core_partials, nblk, c->stream);
         c->launches += 2;
         if (e != cudaSuccess) return cuda_fail(c, e, "core launch");
@@ -688,6 +690,14 @@ sft_status sft_set_slice_tiling(sft_ctx *c, int64_t tile, int64_t max_direct) {
 sft_status sft_set_tensor_cores(sft_ctx *c, int32_t enable) {
     if (!c) return SFT_EINVAL;
     c->tensor_cores = enable ? 1 : 0;
+    return SFT_OK;
+}
+
+sft_status sft_set_tc_wait_limit(sft_ctx *c, int64_t limit_ns) {
+    if (!c) return SFT_EINVAL;
+    if (limit_ns < 0 || limit_ns > 60000000000LL)
+        return fail(c, SFT_EINVAL, "tensor-core wait limit must be in [0, 60 s]");
+    c->tc_wait_ns = (uint64_t)limit_ns;
     return SFT_OK;
 }
 

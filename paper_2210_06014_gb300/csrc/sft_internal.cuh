@@ -65,11 +65,13 @@ int core_blocks_for(int64_t count, int sms);
 // tensor-core (tcgen05) forms of the refresh and the minibatch core gradient
 // for bfloat16 cached products (k_tc.cu)
 bool refresh_tc_supported(int J, int R);
+// wait_ns: time limit of the kernels' waits on their own copies and MMAs
+// (0: give up at once); the drain after an expired wait keeps a 2 s bound.
 cudaError_t launch_refresh_tc(const float *A, const float *B, void *C, int64_t I, int J, int R,
-                              int *err, cudaStream_t st, int sms);
+                              int *err, uint64_t wait_ns, cudaStream_t st, int sms);
 bool core_tc_supported(int J, int R);
 cudaError_t launch_core_tc(const PassArgs &a, int J, int R, float *partials, int nblk,
-                           cudaStream_t st);
+                           uint64_t wait_ns, cudaStream_t st);
 cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
                               float lr, float lam, cudaStream_t st);
 // Streams of one slice factor pass: `tiles` is the caller's stream; `chains`

@@ -9,6 +9,7 @@
 // deterministic = 1) with its scratch -- the per-chunk row sums of a minibatch
 // and the bad-data flag -- in a fixed array of device memory that is part of
 // the library image itself.
+#include <cmath>
 #include <mutex>
 
 #include "sft_internal.cuh"
@@ -68,7 +69,7 @@ extern "C" sft_status sft_update_factors_noalloc(int32_t order, const int64_t *d
     if (order < 2 || order > kMaxOrder || !dims || !J || !C || !idx) return SFT_EINVAL;
     if (mode < 0 || mode >= order) return SFT_EINVAL;
     if (nnz < 0 || nnz > 0x7fffffffLL || batch < 1) return SFT_EINVAL;
-    if (!(lr == lr) || !(lambda == lambda)) return SFT_EINVAL;
+    if (!std::isfinite(lr) || !std::isfinite(lambda)) return SFT_EINVAL;
     auto rank_ok = [](int v) { return v == 4 || v == 8 || v == 16 || v == 32; };
     if (!rank_ok(R) || !rank_ok(J[mode]) || 4 * J[mode] < R) return SFT_ENOTSUP;
     if (batch > kNoallocMaxBatch) return SFT_ENOTSUP;  // the scratch holds 4096-sample batches
@@ -82,9 +83,14 @@ extern "C" sft_status sft_update_factors_noalloc(int32_t order, const int64_t *d
     if (nnz > 0 && !val) return SFT_EINVAL;
     if (nnz == 0) return SFT_OK;
 
+    cudaStream_t st = (cudaStream_t)stream;
+    // The call reads the bad-data flag back and waits for the stream, which a
+    // stream capture cannot hold: refuse before touching anything.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SFT_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SFT_ENOTSUP;
     NoallocScratch *sc = nullptr;
     if (scratch_on_current_device(&sc) != cudaSuccess) return SFT_ECUDA;
-    cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(&sc->err, 0, sizeof(int), st) != cudaSuccess) return SFT_ECUDA;
 
     PassArgs a{};

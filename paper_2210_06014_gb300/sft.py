@@ -37,7 +37,7 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
             "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers",
-            "sft_autotune_slices", "sft_set_tensor_cores"]
+            "sft_autotune_slices", "sft_set_tensor_cores", "sft_set_tc_wait_limit"]
 
 
 class SftError(RuntimeError):
@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
     lib.sft_set_slice_tiling.restype = ctypes.c_int
     lib.sft_set_tensor_cores.argtypes = [ctx, i32]
     lib.sft_set_tensor_cores.restype = ctypes.c_int
+    lib.sft_set_tc_wait_limit.argtypes = [ctx, i64]
+    lib.sft_set_tc_wait_limit.restype = ctypes.c_int
     lib.sft_update_factors_noalloc.argtypes = [
         i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
         ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
@@ -356,6 +358,11 @@ def sft_set_slice_tiling(ctx, tile: int = 0, max_direct: int = 0) -> None:
 def sft_set_tensor_cores(ctx, enable: bool = True) -> None:
     lib = load()
     _check(lib, ctx, lib.sft_set_tensor_cores(ctx, 1 if enable else 0), "sft_set_tensor_cores")
+
+
+def sft_set_tc_wait_limit(ctx, limit_ns: int) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_set_tc_wait_limit(ctx, int(limit_ns)), "sft_set_tc_wait_limit")
 
 
 def sft_update_factors_noalloc(dims, J, R, mode, A_mode, B_mode, C, idx, val, perm, nnz, batch,

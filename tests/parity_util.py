@@ -94,6 +94,37 @@ def assert_within(got, want, scale, tol=TOL32, what=""):
                              f"(err/bound {float(err[i] / bound[i]):.3g})")
 
 
+U32 = 2.0 ** -24  # unit roundoff of float32
+
+
+def assert_rows_within(got, want, S1, S2, tol=TOL32, what=""):
+    """Per-row, per-entry check of a whole factor pass against the oracle.
+
+    S1, S2 come from the oracle's run of the same pass (factor_pass_scaled):
+    S1 sums, over the row's samples, the magnitudes lr ((|x| + |a|.|v|)|v| +
+    lam |a|) that every step's products and sums round against, and S2 sums
+    |a| over the row's steps (each step's add to the row rounds against |a|).
+    Errors made at one step are not amplified by later steps (each step scales
+    a row by 1 - lr |v|^2 along v and by 1 - lr lam elsewhere, both at most 1
+    in size at the learning rates used), so a float32 run -- element by element,
+    or re-associated into products of affine maps -- stays within
+    tol * S1 + 4 u * S2 of the float64 pass entry by entry (u = 2^-24; tol =
+    1e-5 for float32 cached products, 2e-2 for bfloat16).  Rows a pass never
+    visits must come back unchanged."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    bound = tol * np.asarray(S1) + 4.0 * U32 * np.asarray(S2) + 1e-30
+    err = np.abs(got - want)
+    ratio = err / bound
+    if not (ratio <= 1.0).all():
+        i = np.unravel_index(np.argmax(ratio), ratio.shape)
+        bad_rows = int(np.any(ratio > 1.0, axis=1).sum())
+        raise AssertionError(f"{what}: {bad_rows} rows leave their bound; worst at {i}: got "
+                             f"{got[i]!r} want {want[i]!r} bound {bound[i]!r} "
+                             f"(err/bound {float(ratio[i]):.3g})")
+    return float(ratio.max())
+
+
 def rel_fro(got, want):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)

@@ -321,6 +321,104 @@ def test_core_batches_are_sequential(oracle_mod):
 # ----------------------------------------------------------------------------- whole iteration (Algorithm 2)
 
 
+def _written_out_epoch(m, idx, val, pf, pc, bf, bc, lr_A, lam_A, lr_B, lam_B, variant="alg2"):
+    """Algorithm 2's loop body written out from the separately pinned passes:
+    for every mode a factor pass then a refresh of that mode's cached product,
+    then for every mode a core pass then a refresh.  The other variants are
+    plausible misreadings, kept to show that the test tensor tells them apart."""
+    N = m.N
+    if variant == "core_first":
+        for n in range(N):
+            m.core_pass(n, idx, val, perm=pc[n], batch=bc, lr=lr_B, lam=lam_B)
+            m.refresh(n)
+        for n in range(N):
+            m.factor_pass(n, idx, val, perm=pf[n], batch=bf, lr=lr_A, lam=lam_A)
+            m.refresh(n)
+        return
+    for n in range(N):
+        m.factor_pass(n, idx, val, perm=pf[n], batch=bf, lr=lr_A, lam=lam_A)
+        if variant == "no_factor_refresh":
+            continue
+        m.refresh((n + 1) % N if variant == "wrong_mode_refresh" else n)
+    if variant == "no_factor_refresh":
+        m.refresh_all()
+    for n in range(N):
+        m.core_pass(n, idx, val, perm=pc[n], batch=bc, lr=lr_B, lam=lam_B)
+        m.refresh(n)
+
+
+def test_epoch_follows_algorithm2_schedule(oracle_mod):
+    """orc_epoch equals Algorithm 2 written out pass by pass (factor module
+    over every mode, each followed by a refresh of that mode; then the core
+    module likewise), with a distinct permutation per pass, to 1e-14.  The
+    misreadings (modules swapped, a refresh of the wrong mode, no refresh after
+    the factor passes) move the parameters by far more on the same input, so
+    the comparison would catch them."""
+    rng = np.random.default_rng(21)
+    I, J, R = (7, 6, 5), (3, 2, 3), 3
+    A, B = rand_model(rng, I, J, R)
+    idx, val = rand_coo(rng, I, 60)
+    pf = [rng.permutation(60).astype(np.uint32) for _ in range(3)]
+    pc = [rng.permutation(60).astype(np.uint32) for _ in range(3)]
+    args = dict(bf=4, bc=8, lr_A=0.05, lam_A=0.01, lr_B=0.07, lam_B=0.02)
+    got = oracle_mod.Model(A, B)
+    for _ in range(2):  # two epochs: the second starts from the first's result
+        got.epoch(idx, val, pf, pc, batch_factor=args["bf"], batch_core=args["bc"],
+                  lr_A=args["lr_A"], lam_A=args["lam_A"], lr_B=args["lr_B"], lam_B=args["lam_B"])
+    want = oracle_mod.Model(A, B)
+    for _ in range(2):
+        _written_out_epoch(want, idx, val, pf, pc, **args)
+    for n in range(3):
+        np.testing.assert_allclose(got.A[n], want.A[n], rtol=1e-14, atol=1e-16)
+        np.testing.assert_allclose(got.B[n], want.B[n], rtol=1e-14, atol=1e-16)
+        np.testing.assert_allclose(got.C[n], want.C[n], rtol=1e-14, atol=1e-16)
+    for variant in ("core_first", "wrong_mode_refresh", "no_factor_refresh"):
+        wrong = oracle_mod.Model(A, B)
+        for _ in range(2):
+            _written_out_epoch(wrong, idx, val, pf, pc, variant=variant, **args)
+        diff = max(float(np.abs(wrong.A[n] - want.A[n]).max()) for n in range(3))
+        diff = max(diff, max(float(np.abs(wrong.B[n] - want.B[n]).max()) for n in range(3)))
+        assert diff > 1e-6, variant
+
+
+def test_factor_pass_rounding_scale(oracle_mod):
+    """The rounding scales returned with a factor pass are the sums they are
+    documented to be, re-derived here by stepping the pass in numpy (batch 1):
+    S1 = sum_s lr((|x| + |a|.|v|)|v| + lam |a|) with |v| = |B^(n)| prod |A||B|
+    rows, S2 = sum_s |a| at each step; the pass itself is unchanged."""
+    rng = np.random.default_rng(22)
+    I, J, R = (5, 4, 3), (2, 3, 2), 3
+    A, B = rand_model(rng, I, J, R)
+    idx, val = rand_coo(rng, I, 30)
+    n, lr, lam = 1, 0.1, 0.02
+    m = oracle_mod.Model(A, B)
+    S1, S2 = m.factor_pass_scaled(n, idx, val, batch=1, lr=lr, lam=lam)
+    plain = oracle_mod.Model(A, B)
+    plain.factor_pass(n, idx, val, batch=1, lr=lr, lam=lam)
+    np.testing.assert_array_equal(m.A[n], plain.A[n])
+    a = A[n].copy()
+    C = [x @ y for x, y in zip(A, B)]
+    absC = [np.abs(x) @ np.abs(y) for x, y in zip(A, B)]
+    w1, w2 = np.zeros_like(a), np.zeros_like(a)
+    for s in range(len(val)):
+        i = idx[n][s]
+        p = np.ones(R)
+        pa = np.ones(R)
+        for k in range(3):
+            if k != n:
+                p *= C[k][idx[k][s]]
+                pa *= absC[k][idx[k][s]]
+        v = B[n] @ p
+        va = np.abs(B[n]) @ pa
+        e = float(val[s]) - a[i] @ v
+        w1[i] += lr * ((abs(float(val[s])) + np.abs(a[i]) @ va) * va + lam * np.abs(a[i]))
+        w2[i] += np.abs(a[i])
+        a[i] = a[i] + lr * (e * v - lam * a[i])
+    np.testing.assert_allclose(S1, w1, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(S2, w2, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(m.A[n], a, rtol=1e-12, atol=1e-15)
+
+
 @pytest.mark.slow
 def test_planted_recovery(oracle_mod):
     """A noise-free planted J=R=3 model on a well-sampled 30x30x30 tensor is

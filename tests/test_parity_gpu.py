@@ -10,7 +10,8 @@ import pytest
 import torch
 
 from parity_util import (TOL32, abs_C, assert_within, core_step_scale, factor_step_scale,
-                         np_idx, pred_scale, rel_fro, small_tensor, to_dev)
+                         np_idx, pred_scale, rel_fro, small_tensor, to_dev,
+                         assert_rows_within)
 
 pytestmark = pytest.mark.gpu
 
@@ -125,9 +126,11 @@ def test_factor_pass_perm_ragged(sft, oracle_mod):
     dec.update_factors(n, idx, val, perm.cuda(), batch=4096, lr=0.05, lam=0.01)
     dec.sync(60_000)
     ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
-    ref.factor_pass(n, np_idx(T.idx), T.val.numpy(), perm=perm.numpy().astype(np.uint32),
-                    batch=4096, lr=0.05, lam=0.01)
+    S1, S2 = ref.factor_pass_scaled(n, np_idx(T.idx), T.val.numpy(),
+                                    perm=perm.numpy().astype(np.uint32), batch=4096, lr=0.05,
+                                    lam=0.01)
     got = dec.A[n].cpu().numpy().astype(np.float64)
+    assert_rows_within(got, ref.A[n], S1, S2, what="ragged minibatch pass")
     assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4
     assert rel_fro(got, ref.A[n]) < TOL32
 

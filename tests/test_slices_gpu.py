@@ -14,8 +14,8 @@ import numpy as np
 import pytest
 import torch
 
-from parity_util import (TOL32, assert_within, core_step_scale, np_idx, rel_fro, small_tensor,
-                         to_dev)
+from parity_util import (TOL32, assert_rows_within, assert_within, core_step_scale, np_idx,
+                         rel_fro, small_tensor, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -82,9 +82,11 @@ def test_factor_slices_equal_sequential_pass(sft, oracle_mod, tiling):
         sl = dec.slices(n, idx, val, perm.cuda())
         dec.update_factors_slices(sl, lr=0.05, lam=0.01)
         dec.sync(60_000)
-        ref.factor_pass(n, ix, T.val.numpy(), perm=perm.numpy().astype(np.uint32), batch=1,
-                        lr=0.05, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(),
+                                        perm=perm.numpy().astype(np.uint32), batch=1, lr=0.05,
+                                        lam=0.01)
         got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert_rows_within(got, ref.A[n], S1, S2, what=f"tiling {tiling} A^({n})")
         assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n
         # keep both sides on the same parameters for the next mode
@@ -109,9 +111,12 @@ def test_factor_slices_skewed_tensor(sft, oracle_mod, skewed):
         sl = dec.slices(n, idx, val, None)
         dec.update_factors_slices(sl, lr=0.01, lam=0.01)
         dec.sync(60_000)
-        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01,
+                                        lam=0.01)
         got = dec.A[n].cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(got))
+        worst = assert_rows_within(got, ref.A[n], S1, S2, what=f"skewed A^({n})")
+        print(f"skewed mode {n}: worst err/bound {worst:.3g}")
         assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n
 
@@ -156,11 +161,13 @@ def test_high_order_slice_passes(sft, oracle_mod, name, tiling):
         dec.update_factors_slices(sl, lr=lr, lam=0.01)
         dec.refresh(n)
         dec.sync(60_000)
-        ref.factor_pass(n, ix, T.val.numpy(), perm=perm.numpy().astype(np.uint32), batch=1,
-                        lr=lr, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(),
+                                        perm=perm.numpy().astype(np.uint32), batch=1, lr=lr,
+                                        lam=0.01)
         ref.refresh(n)
         got = dec.A[n].cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(got)), n
+        assert_rows_within(got, ref.A[n], S1, S2, what=f"{name} {tiling} A^({n})")
         # A row takes L = nnz / I_n dependent float32 steps on average; the
         # slice path re-associates them (maps, products of maps), so its
         # rounding is bounded by a small multiple of L u (u = 2^-24) relative
@@ -347,10 +354,12 @@ def test_bf16_slice_passes(sft, oracle_mod):
         sl = dec.slices(n, idx, val, None)
         dec.update_factors_slices(sl, lr=0.05, lam=0.01)
         dec.refresh(n)
-        ref.factor_pass(n, ix, T.val.numpy(), batch=1, lr=0.05, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), batch=1, lr=0.05, lam=0.01)
         ref.refresh(n)
         dec.sync(60_000)
         got = dec.A[n].cpu().numpy().astype(np.float64)
+        worst = assert_rows_within(got, ref.A[n], S1, S2, tol=TOL_BF16, what=f"bf16 A^({n})")
+        print(f"bf16 factor pass mode {n}: worst err/bound {worst:.3g}")
         assert rel_fro(got - A0, ref.A[n] - A0) < TOL_BF16, n
     for n in range(3):
         B0 = dec.B[n].cpu().numpy().astype(np.float64)
@@ -468,8 +477,10 @@ def test_fiber_pass_on_skewed_tensor_matches_oracle(sft, oracle_mod, skewed):
         assert 0 < nf <= T.nnz
         dec.update_factors_slices(sl, lr=0.01, lam=0.01)
         dec.sync(60_000)
-        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01,
+                                        lam=0.01)
         got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert_rows_within(got, ref.A[n], S1, S2, what=f"fibers skewed A^({n})")
         assert rel_fro(got - A0, ref.A[n] - A0) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n
 
@@ -520,8 +531,10 @@ def test_slice_autotune_leaves_A_and_keeps_parity(sft, oracle_mod, skewed, fiber
         assert L == 2 * W or L in (1024, 2048, 4096, 8192, 16384, 1 << 40)
         dec.update_factors_slices(sl, lr=0.01, lam=0.01)
         dec.sync(60_000)
-        ref.factor_pass(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01, lam=0.01)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01,
+                                        lam=0.01)
         got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert_rows_within(got, ref.A[n], S1, S2, what=f"autotuned (fibers={fibers}) A^({n})")
         A0n = A0.cpu().numpy().astype(np.float64)
         assert rel_fro(got - A0n, ref.A[n] - A0n) < 1e-4, n
         assert rel_fro(got, ref.A[n]) < TOL32, n

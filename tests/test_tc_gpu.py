@@ -160,3 +160,56 @@ def test_tc_epochs_rmse(sft, oracle_mod):
         want.append(ref.rmse(ix, xv))
     print("tensor-core epochs rmse gpu", got, "oracle", want)
     np.testing.assert_allclose(got, want, rtol=0.01)
+
+
+# ----------------------------------------------------------------------------- bounded waits
+
+
+def test_tc_wait_expiry_is_reported_and_recoverable(sft, oracle_mod):
+    """The expiry path of the tensor-core kernels' bounded waits, made to run on
+    a normal launch: with a wait limit of 0 every block gives up at its first
+    wait on its own TMA copy / MMA, flags it, drains what it issued (full 2 s
+    bound), frees its tensor memory and returns.  sft_sync reports
+    SFT_ETIMEOUT for the refresh and for the core pass; with the default limit
+    restored, the same context refreshes C and takes a core step that match
+    the oracle again.  Nothing faults or hangs: every wait stays bounded."""
+    T = planted(16, 16, dims=(1031, 517, 77), nnz=20_000, seed=3)
+    idx, val = to_dev(T)
+    n, lr, lam = 1, 1.0, 0.01
+    dec = sft.Decomposition(T.A0, T.B0, prec=sft.SFT_BF16, tensor_cores=True)
+    dec.sync(60_000)
+    B_keep = [b.clone() for b in dec.B]
+    sft.sft_set_tc_wait_limit(dec.ctx, 0)
+    dec.refresh(-1)
+    with pytest.raises(sft.SftError) as ex:
+        dec.sync(60_000)
+    assert ex.value.status == sft.SFT_ETIMEOUT
+    dec.update_core(n, idx, val, None, batch=4096, lr=lr, lam=lam)
+    with pytest.raises(sft.SftError) as ex:
+        dec.sync(60_000)
+    assert ex.value.status == sft.SFT_ETIMEOUT
+    # back to the default limit: the context is usable and the results are right
+    sft.sft_set_tc_wait_limit(dec.ctx, 2_000_000_000)
+    for k in range(3):
+        dec.B[k].copy_(B_keep[k])
+    dec.refresh(-1)
+    dec.sync(60_000)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    absC = abs_C(ref.A, ref.B)
+    for k in range(3):
+        assert_within(dec.C[k].float().cpu().numpy(), ref.C[k], absC[k], tol=TOL_BF16,
+                      what=f"C^({k}) after the expired waits")
+    M = 4096
+    sub_idx = [i[:M].contiguous() for i in idx]
+    sub_val = val[:M].contiguous()
+    B_before = dec.B[n].cpu().numpy().astype(np.float64)
+    dec.update_core(n, sub_idx, sub_val, None, batch=M, lr=lr, lam=lam)
+    dec.sync(60_000)
+    got = dec.B[n].cpu().numpy().astype(np.float64) - B_before
+    ix = np_idx(T.idx)
+    sel = np.arange(M)
+    ref.core_pass(n, [i[sel] for i in ix], T.val.numpy()[sel], batch=M, lr=lr, lam=lam)
+    want = ref.B[n] - np.asarray(T.B0[n], dtype=np.float64)
+    scale = core_step_scale(ref.A, [b.numpy().astype(np.float64) for b in T.B0], n, ix,
+                            T.val.numpy(), sel, lr, lam)
+    assert_within(got, want, scale, tol=TOL_BF16, what="core step after the expired waits")
