@@ -68,6 +68,12 @@ def parse():
     p.add_argument("--fibers", default="auto", choices=["auto", "on", "off"],
                    help="form v once per fiber (tuple of the other modes' coordinates) in the "
                         "factor pass: on, off, or auto = for modes with at most nnz/2 fibers")
+    p.add_argument("--epochs-rmse", type=int, default=10,
+                   help="epochs of the per-epoch test-RMSE curves (float32 and bfloat16 C, "
+                        "same init; 0 = skip the curves and the bfloat16 block)")
+    p.add_argument("--no-e2e-raw", action="store_true",
+                   help="skip the end-to-end figure that rebuilds the slice layouts and fiber "
+                        "tables from raw COO every step")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
     p.add_argument("--slice-max-direct", type=int, default=0,
                    help="longest crossing slice run element by element (0 = automatic)")
@@ -434,6 +440,8 @@ def run_batch(args, world, rank, lr):
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
+            "e2e_raw": e2e_raw,
+            "precision_and_convergence": conv,
             "cpu_baseline": cpu,
         }))
     if world > 1:
@@ -622,6 +630,8 @@ def run_autograd(args, world, rank, sft, T, spec, metric, unit, gen_s):
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
+            "e2e_raw": e2e_raw,
+            "precision_and_convergence": conv,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -775,11 +785,13 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     resident = {"slices": slices, "idx": idx, "val": val, "tidx": tidx, "tval": tval,
                 "ready": None}
 
-    def step(timed: bool, inp=resident):
-        """One epoch over the inputs `inp`.  inp["ready"]: None, or per mode and
-        for the test set a list of events recorded after that input's
-        host-to-device copies; the step waits on them before it first reads
-        that input."""
+    def step(timed: bool, inp=resident, d=None, lout=None):
+        """One epoch over the inputs `inp` on decomposition d (default: dec).
+        inp["ready"]: None, or per mode and for the test set a list of events
+        recorded after that input's host-to-device copies; the step waits on
+        them before it first reads that input."""
+        d = d or dec
+        lout = loss_out if lout is None else lout
         ready = inp["ready"]
         sls = inp["slices"]
         def wait_ready(i):
@@ -793,14 +805,14 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 a, b = ev_pair("factor")
                 a.record(stream)
             if sls:
-                dec.update_factors_slices(sls[n], lr=lr, lam=0.01)
+                d.update_factors_slices(sls[n], lr=lr, lam=0.01)
             else:
-                dec.update_factors(n, inp["idx"], inp["val"], None, batch=4096, lr=lr, lam=0.01)
+                d.update_factors(n, inp["idx"], inp["val"], None, batch=4096, lr=lr, lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
                 a.record(stream)
-            dec.refresh(n)
+            d.refresh(n)
             if timed:
                 b.record(stream)
         for n in range(N):
@@ -808,22 +820,22 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 a, b = ev_pair("core")
                 a.record(stream)
             if sls:
-                dec.update_core_slices(sls[n], batch=core_batch, lr=lr, lam=0.01)
+                d.update_core_slices(sls[n], batch=core_batch, lr=lr, lam=0.01)
             else:
-                dec.update_core(n, inp["idx"], inp["val"], None, batch=core_batch, lr=lr,
+                d.update_core(n, inp["idx"], inp["val"], None, batch=core_batch, lr=lr,
                                 lam=0.01)
             if timed:
                 b.record(stream)
                 a, b = ev_pair("refresh")
                 a.record(stream)
-            dec.refresh(n)
+            d.refresh(n)
             if timed:
                 b.record(stream)
         wait_ready(N)
         if timed:
             a, b = ev_pair("loss")
             a.record(stream)
-        sft.sft_loss_async(dec.ctx, inp["tidx"], inp["tval"], ntest, loss_out)
+        sft.sft_loss_async(d.ctx, inp["tidx"], inp["tval"], ntest, lout)
         if timed:
             b.record(stream)
 
@@ -984,6 +996,112 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                "d2h_bytes_per_step": 16}
         del sets[1]
 
+    # end to end from raw COO: every step copies the raw training and test sets
+    # from pinned host memory, builds the slice layout and fiber table of
+    # every mode on the device (the preprocessing the headline leaves out, as
+    # the paper does for B-CSF), runs the epoch and reads the loss back
+    e2e_raw = None
+    if slices and not args.no_e2e and not args.no_e2e_raw:
+        hraw = [t.cpu().pin_memory() for t in list(idx) + [val] + list(tidx) + [tval]]
+        draw = [torch.empty_like(t) for t in list(idx) + [val] + list(tidx) + [tval]]
+        hloss2 = torch.zeros(2, dtype=torch.float64).pin_memory()
+        use_f = [sl.fid is not None for sl in slices]
+        use_p = [sl.P is not None for sl in slices]
+
+        def raw_step():
+            for dd, hh in zip(draw, hraw):
+                dd.copy_(hh, non_blocking=True)
+            ridx, rval = draw[:N], draw[N]
+            lays = [dec.slices(n, ridx, rval, None) for n in range(N)]
+            for n, sl in enumerate(lays):
+                sl._scratch = None
+                if use_f[n]:
+                    sl.build_fibers(dec, core=use_p[n])
+            inp = {"slices": lays, "idx": ridx, "val": rval, "tidx": draw[N + 1:2 * N + 1],
+                   "tval": draw[2 * N + 1], "ready": None}
+            step(False, inp)
+            hloss2.copy_(loss_out, non_blocking=True)
+
+        raw_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            raw_step()
+        torch.cuda.synchronize()
+        rt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e_raw = {"value": total_nnz / rt, "unit": unit,
+                   "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in hraw)),
+                   "d2h_bytes_per_step": 16,
+                   "what": "epoch plus, every step, the host-to-device copy of the raw COO "
+                           "train and test sets and the device build of every mode's slice "
+                           "layout and fiber table (host wall clock over the steps)"}
+        del draw, hraw
+
+    # precision block and convergence curves: the same epoch with bfloat16
+    # cached products (timed like the headline, from the initial parameters),
+    # and the test RMSE after each of `epochs_rmse` epochs from the same
+    # initial parameters for both storages of C (untimed)
+    conv = None
+    if args.epochs_rmse > 0 and rank == 0 and world == 1:
+        def fresh(prec_c):
+            d = sft.Decomposition(T.A0, T.B0, deterministic=False, max_batch=4096, prec=prec_c)
+            if slices:
+                d.set_slice_tiling(args.slice_tile, args.slice_max_direct)
+                if chain_limits:
+                    for sl in slices:
+                        d.autotune_slices(sl, lr=lr, lam=0.01)
+            return d
+
+        other = sft.SFT_BF16 if prec == sft.SFT_FP32 else sft.SFT_FP32
+        other_name = "bf16" if other == sft.SFT_BF16 else "fp32"
+        lo = torch.zeros(2, dtype=torch.float64, device=dev)
+        d_o = fresh(other)
+        for _ in range(args.warmup):
+            step(False, d=d_o, lout=lo)
+        torch.cuda.synchronize()
+        ev.clear()
+        s3, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s3.record(stream)
+        for _ in range(args.steps):
+            step(True, d=d_o, lout=lo)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        o_elapsed = s3.elapsed_time(e3) / 1e3
+        of_ms, _ = avg_ms("factor", N)
+        oc_ms, _ = avg_ms("core", N)
+        o_cb = 2 if other == sft.SFT_BF16 else 4
+        o_fac, _ = algorithmic_bytes(N, J, R, args.path, rows_per_nnz, o_cb)
+        d_o.close()
+        del d_o
+        curves = {}
+        for name, pc in ((args.prec, prec), (other_name, other)):
+            d = fresh(pc)
+            ys = []
+            for _ in range(args.epochs_rmse):
+                step(False, d=d, lout=lo)
+                sse_e, _ = lo.tolist()
+                ys.append((sse_e / ntest) ** 0.5 if ntest else None)
+            curves[name] = ys
+            d.close()
+            del d
+        conv = {
+            other_name: {"value": nnz * args.steps / o_elapsed, "unit": unit,
+                         "ms_per_step": o_elapsed / args.steps * 1e3,
+                         "per_launch_ms": {"factor": of_ms, "core": oc_ms},
+                         "c_storage": other_name},
+            "test_rmse_per_epoch": curves,
+            "epochs": args.epochs_rmse,
+            "final_rmse_ratio_bf16_over_fp32": (curves["bf16"][-1] / curves["fp32"][-1]
+                                                if curves["fp32"][-1] else None),
+            "speedup_bf16_over_fp32": (
+                (nnz * args.steps / o_elapsed) / value if other == sft.SFT_BF16
+                else value / (nnz * args.steps / o_elapsed)),
+            "what": "test RMSE after each epoch from the same initial parameters "
+                    "(Section 'Real-world accuracy'); the other storage of C timed like "
+                    "the headline",
+        }
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, S = cpu_oracle_epoch_rate(T, args.cpu_sample)
@@ -1025,6 +1143,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
+            "e2e_raw": e2e_raw,
+            "precision_and_convergence": conv,
             "cpu_baseline": cpu,
         }
         if print_line:

@@ -579,17 +579,34 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         pw = ainv;
     };
     auto apply = [&](const float (&v)[J], const float (&vl)[JL], float x, bool ok) {
-        // w = v^T M' on the lane's columns (two partial sums each)
+        // w = v^T M' on the lane's columns (two partial sums each); columns are
+        // taken in pairs with packed float32 FMAs (each half is an ordinary
+        // fused multiply-add, so the sums are the same as column by column)
         float w[JC];
+        if constexpr (JC % 2 == 0) {
 #pragma unroll
-        for (int k = 0; k < JC; ++k) {
-            float e0 = 0.f, e1 = 0.f;
+            for (int k = 0; k < JC; k += 2) {
+                float2 e0 = make_float2(0.f, 0.f), e1 = e0;
 #pragma unroll
-            for (int q = 0; q < J; q += 2) {
-                e0 = fmaf(v[q], M[q][k], e0);
-                e1 = fmaf(v[q + 1], M[q + 1][k], e1);
+                for (int q = 0; q < J; q += 2) {
+                    e0 = __ffma2_rn(make_float2(v[q], v[q]), make_float2(M[q][k], M[q][k + 1]), e0);
+                    e1 = __ffma2_rn(make_float2(v[q + 1], v[q + 1]),
+                                    make_float2(M[q + 1][k], M[q + 1][k + 1]), e1);
+                }
+                w[k] = e0.x + e1.x;
+                w[k + 1] = e0.y + e1.y;
             }
-            w[k] = e0 + e1;
+        } else {
+#pragma unroll
+            for (int k = 0; k < JC; ++k) {
+                float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < J; q += 2) {
+                    e0 = fmaf(v[q], M[q][k], e0);
+                    e1 = fmaf(v[q + 1], M[q + 1][k], e1);
+                }
+                w[k] = e0 + e1;
+            }
         }
         float sc = 0.f;
 #pragma unroll
@@ -600,10 +617,24 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
             const float ns = nvc * sc;
 #pragma unroll
             for (int k = 0; k < JC; ++k) w[k] *= nvc;
+            if constexpr (JC % 2 == 0) {
 #pragma unroll
-            for (int q = 0; q < J; ++q) {
+                for (int q = 0; q < J; ++q) {
 #pragma unroll
-                for (int k = 0; k < JC; ++k) M[q][k] = fmaf(v[q], w[k], M[q][k]);
+                    for (int k = 0; k < JC; k += 2) {
+                        const float2 r = __ffma2_rn(make_float2(v[q], v[q]),
+                                                    make_float2(w[k], w[k + 1]),
+                                                    make_float2(M[q][k], M[q][k + 1]));
+                        M[q][k] = r.x;
+                        M[q][k + 1] = r.y;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < J; ++q) {
+#pragma unroll
+                    for (int k = 0; k < JC; ++k) M[q][k] = fmaf(v[q], w[k], M[q][k]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < JL; ++q) cv[q] = fmaf(xs, vl[q], fmaf(vl[q], ns, cv[q]));
