@@ -74,6 +74,9 @@ def parse():
     p.add_argument("--no-e2e-raw", action="store_true",
                    help="skip the end-to-end figure that rebuilds the slice layouts and fiber "
                         "tables from raw COO every step")
+    p.add_argument("--long-slices", default="maps", choices=["maps", "subslices"],
+                   help="long slices exactly through composed maps (Algorithm 4 order), or as "
+                        "concurrent sub-slices merged with atomic adds (the paper's B-CSF manner)")
     p.add_argument("--slice-tile", type=int, default=0, help="slice tile length (0 = automatic)")
     p.add_argument("--slice-max-direct", type=int, default=0,
                    help="longest crossing slice run element by element (0 = automatic)")
@@ -743,6 +746,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     rows_per_nnz = 1.0
     if args.path == "slices":
         dec.set_slice_tiling(args.slice_tile, args.slice_max_direct)
+        if args.long_slices == "subslices":
+            dec.set_long_slices(sft.SFT_LONG_SUBSLICES)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         slices = [dec.slices(n, idx, val, None) for n in range(N)]
@@ -868,6 +873,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         return sum(xs) / len(xs), sum(xs) / args.steps
 
     f_ms, f_step = avg_ms("factor", N)
+    f_mode = [sum(a.elapsed_time(b) for a, b in ev["factor"][k::N]) / args.steps
+              for k in range(N)]
+    c_mode = [sum(a.elapsed_time(b) for a, b in ev["core"][k::N]) / args.steps
+              for k in range(N)]
     c_ms, c_step = avg_ms("core", N)
     r_ms, r_step = avg_ms("refresh", 2 * N)
     l_ms, l_step = avg_ms("loss", 1)
@@ -1048,6 +1057,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             d = sft.Decomposition(T.A0, T.B0, deterministic=False, max_batch=4096, prec=prec_c)
             if slices:
                 d.set_slice_tiling(args.slice_tile, args.slice_max_direct)
+                if args.long_slices == "subslices":
+                    d.set_long_slices(sft.SFT_LONG_SUBSLICES)
                 if chain_limits:
                     for sl in slices:
                         d.autotune_slices(sl, lr=lr, lam=0.01)
@@ -1119,6 +1130,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "lr": lr, "lambda": 0.01,
                 "parallelism": "replicas only" if world > 1 else "single GPU",
                 "path": args.path,
+                "long_slices": args.long_slices if args.path == "slices" else None,
                 "schedule": ("factor: every mode-n slice element by element (Algorithm 4 order, "
                              "slice layout)" if slices else "factor: Hogwild rows (COO)")
                             + f"; core: batch {core_batch} (Algorithm 5 when = nnz); refresh "
@@ -1130,6 +1142,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "l2": "inputs larger than L2 (COO 1.6 GB)", "generation_s": round(gen_s, 2),
                 "test_rmse_after": test_rmse,
                 "per_launch_ms": {"factor": f_ms, "core": c_ms, "refresh": r_ms, "loss": l_ms},
+                "per_mode_ms": {"factor": f_mode, "core": c_mode},
                 "per_step_ms": {"factor": f_step, "core": c_step, "refresh": r_step,
                                 "loss": l_step},
                 "algorithmic_bytes_per_nnz": {"factor": fac_epoch / (N * nnz),

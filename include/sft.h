@@ -282,10 +282,13 @@ sft_status sft_update_core_fibers(sft_ctx *ctx, int32_t mode, const int32_t *con
                                   float lr, float lambda);
 
 /* Tiling of the slice passes: tile = positions per work item (0 = automatic),
- * max_direct = longest slice that crosses a tile boundary and is still run
- * element by element by one lane group (0 = automatic, < 0 = none: every
- * crossing slice is split into maps).  Results do not depend on it beyond
- * rounding. */
+ * max_direct = chain length: a slice that crosses a tile boundary and has at
+ * most max_direct nonzeros is run element by element, whole, by one lane
+ * group; a longer one runs its first max_direct nonzeros that way and the rest
+ * through composed affine maps applied to the row the head leaves
+ * (0 = automatic, two tiles; < 0 = none: every crossing slice goes through
+ * maps; values between 0 and one tile are raised to one tile).  Results do
+ * not depend on it beyond rounding. */
 sft_status sft_set_slice_tiling(sft_ctx *ctx, int64_t tile, int64_t max_direct);
 
 /* Tensor cores for the two dense contractions when the cached products are
@@ -316,10 +319,26 @@ sft_status sft_set_tensor_cores(sft_ctx *ctx, int32_t enable);
  * it is tested).  Does not affect the float32 kernels. */
 sft_status sft_set_tc_wait_limit(sft_ctx *ctx, int64_t limit_ns);
 
+/* How the slice factor pass runs a long slice (a crossing slice longer than
+ * max_direct):
+ *   SFT_LONG_MAPS (default): exactly, in Algorithm 4's element order -- its
+ *     first max_direct nonzeros as a chain, the rest cut at tile boundaries
+ *     into pieces composed as affine maps and applied in order;
+ *   SFT_LONG_SUBSLICES: as the paper's B-CSF storage treats a heavy slice
+ *     (Section "Tensor Storage Format"; its sub-slices are walked
+ *     concurrently): every tile-sized piece is walked element by element from
+ *     the row as it stands when the walk starts, and its change is added to
+ *     the row with atomic adds.  Pieces of one row overlap in time (Hogwild
+ *     within the row), so the result depends on scheduling. */
+#define SFT_LONG_MAPS 0
+#define SFT_LONG_SUBSLICES 1
+sft_status sft_set_long_slices(sft_ctx *ctx, int32_t how);
+
 /* Per-mode autotuner of the slice factor pass: times the pass of `mode` with
  * several limits on the length of a crossing slice that is run whole as one
- * chain (2W, 1024 .. 16384, and every crossing slice; longer ones go through
- * maps) and keeps the fastest for this mode.  It overrides the tiling's
+ * chain (2W, 1024 .. 65536, and every crossing slice whole; a longer slice
+ * runs that many nonzeros as a chain and the rest through maps) and keeps the
+ * fastest for this mode.  It overrides the tiling's
  * max_direct for that mode until sft_set_slice_tiling is called again.  Every
  * trial starts from the same A^(mode): it is saved to scratch (DEVICE,
  * >= I_mode * J_mode floats, 16-byte aligned) first and restored after each

@@ -340,7 +340,8 @@ static FiberCoords fiber_coords(const PassArgs &a, const int32_t *const *fcoord)
 }
 
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, const int32_t *fid, const int32_t *const *fcoord,
+                                 bool subslices, float *maps, const int32_t *fid,
+                                 const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss_in,
                                  int sms, int64_t *launches) {
     SliceStreams ss = ss_in;
@@ -379,6 +380,8 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.row_ptr = row_ptr;
     g.W = W;
     g.Lseq = Lseq;
+    g.Lhead = subslices ? 0 : Lseq;
+    g.subslices = subslices ? 1 : 0;
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     g.fid = fid;
@@ -397,7 +400,7 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
         cudaStreamWaitEvent(st, ss.chains_done, 0);
         cudaStreamWaitEvent(st, ss.maps_done, 0);
     }
-    if (with_maps && g.ntiles > 1) {
+    if (with_maps && !subslices && g.ntiles > 1) {
         cudaError_t e = launch_slice_combine(g, J, R, st, sms);
         *launches += 2;
         if (e != cudaSuccess) return e;

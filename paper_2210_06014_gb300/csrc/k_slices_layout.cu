@@ -192,23 +192,16 @@ __device__ __forceinline__ int64_t block_len(int64_t K) {
     return b < 1 ? 1 : b;
 }
 
-__device__ __forceinline__ int piece_slot(int64_t s, int64_t t, int64_t W) { return s < t * W ? 0 : 1; }
+// Slot of a long slice's piece in tile t, its map region starting at hs.
+__device__ __forceinline__ int piece_slot(int64_t hs, int64_t t, int64_t W) {
+    return hs < t * W ? 0 : 1;
+}
 
-// The long slice whose piece in tile t is on `side` (0: run that started before
-// the tile, 1: run that starts in the tile and continues after it).
+// The long slice whose map piece in tile t is in slot `side` (see map_piece).
 __device__ __forceinline__ bool long_piece(const SliceArgs &g, int64_t t, int side, int32_t &r,
-                                           int64_t &s, int64_t &e) {
-    const int64_t p0 = t * g.W;
-    const int64_t p1 = min(g.a.nnz, p0 + g.W);
-    const int64_t at = side == 0 ? p0 : p1 - 1;
-    r = __ldg(g.a.idx[g.a.n] + at);
-    if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) return false;
-    s = __ldg(g.row_ptr + r);
-    e = __ldg(g.row_ptr + r + 1);
-    if (!slice_ok(g, s, e) || at < s || at >= e) return false;
-    if (e - s <= g.Lseq) return false;
-    const bool before = s < p0, after = e > p1;
-    return side == 0 ? before : (after && !before);
+                                           int64_t &s, int64_t &e, int64_t &hs) {
+    int64_t q0, q1;
+    return map_piece(g, t, side, r, s, e, hs, q0, q1);
 }
 
 constexpr int kComposeGroups = 8;  // lane groups per block of k_slices_compose
@@ -233,14 +226,14 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose_sme
     for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
         for (int side = 0; side < 2; ++side) {
             int32_t r;
-            int64_t s, e;
-            if (!long_piece(g, t, side, r, s, e)) continue;
-            const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
+            int64_t s, e, hs;
+            if (!long_piece(g, t, side, r, s, e, hs)) continue;
+            const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
             const int64_t Bc = block_len(t1 - t0 + 1);
             if ((t - t0) % Bc != 0) continue;
             const int64_t tl = min(t + Bc - 1, t1);
             if (tl == t) continue;  // a block of one piece is already its own map
-            const float *P = g.maps + (tl * 2 + piece_slot(s, tl, g.W)) * (int64_t)MS;
+            const float *P = g.maps + (tl * 2 + piece_slot(hs, tl, g.W)) * (int64_t)MS;
             for (int j = 0; j < J; ++j)
 #pragma unroll
                 for (int q = 0; q < JL; ++q) X[j * J + sub * JL + q] = __ldcg(P + j * J + sub * JL + q);
@@ -248,7 +241,7 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose_sme
             for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = __ldcg(P + J * J + sub * JL + q);
             __syncwarp(m);
             for (int64_t u = tl - 1; u >= t; --u) {
-                P = g.maps + (u * 2 + piece_slot(s, u, g.W)) * (int64_t)MS;
+                P = g.maps + (u * 2 + piece_slot(hs, u, g.W)) * (int64_t)MS;
                 float pc[J];          // all of P.c
                 float pm[J][JL];      // the lane's columns of P.M
 #pragma unroll
@@ -288,7 +281,7 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose_sme
                 for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = nc[q];
                 __syncwarp(m);
             }
-            float *out = g.maps + (t * 2 + piece_slot(s, t, g.W)) * (int64_t)MS;
+            float *out = g.maps + (t * 2 + piece_slot(hs, t, g.W)) * (int64_t)MS;
             for (int j = 0; j < J; ++j)
 #pragma unroll
                 for (int q = 0; q < JL; ++q) out[j * J + sub * JL + q] = X[j * J + sub * JL + q];
@@ -328,15 +321,15 @@ __global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(Sli
     for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
         for (int side = 0; side < 2; ++side) {
             int32_t r;
-            int64_t s, e;
-            if (!long_piece(g, t, side, r, s, e)) continue;
-            const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
+            int64_t s, e, hs;
+            if (!long_piece(g, t, side, r, s, e, hs)) continue;
+            const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
             const int64_t Bc = block_len(t1 - t0 + 1);
             if ((t - t0) % Bc != 0) continue;
             const int64_t tl = min(t + Bc - 1, t1);
             if (tl == t) continue;  // a block of one piece is already its own map
             auto map_of = [&](int64_t u) {
-                return g.maps + (u * 2 + piece_slot(s, u, g.W)) * (int64_t)MS;
+                return g.maps + (u * 2 + piece_slot(hs, u, g.W)) * (int64_t)MS;
             };
             stage(map_of(tl - 1), buf);
             float X[JL][J], Xc[JL];
@@ -416,13 +409,16 @@ __global__ void __launch_bounds__(kSliceThreads) k_slices_combine(SliceArgs g) {
         int32_t r;
         int64_t s, e;
         if (!first_boundary_slice(g, item + 1, r, s, e) || e - s <= g.Lseq) continue;
+        // the row after the slice's head (run by the chain kernel), then the
+        // block maps of its map region [hs, e) in order
         float *arow = g.a.A + (int64_t)r * J + sub * JL;
         float av[JL];
         load_run<JL>(arow, av);
-        const int64_t t0 = s / g.W, t1 = (e - 1) / g.W;
+        const int64_t hs = s + g.Lhead;
+        const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
         const int64_t Bc = block_len(t1 - t0 + 1);
         for (int64_t t = t0; t <= t1; t += Bc) {
-            const float *mp = g.maps + (t * 2 + piece_slot(s, t, g.W)) * (int64_t)MS;
+            const float *mp = g.maps + (t * 2 + piece_slot(hs, t, g.W)) * (int64_t)MS;
             float full[J];
 #pragma unroll
             for (int k = 0; k < J; ++k) full[k] = __shfl_sync(m, av[k % JL], k / JL, T);
@@ -476,13 +472,16 @@ int slice_core_tile_length(int64_t nnz, int sms) {
 }
 
 // The pass's chain list: every crossing slice (one that spans a tile
-// boundary) with at most Lseq nonzeros.
+// boundary) of at most Lseq nonzeros, and, when long slices have a head
+// (Lhead > 0), every longer crossing slice too (for its head).
 __global__ void k_chain_list(const int32_t *__restrict__ row_ptr, int32_t In, int64_t W,
-                             int64_t Lseq, int64_t nnz, int32_t *list, unsigned int *count) {
+                             int64_t Lseq, int64_t Lhead, int64_t nnz, int32_t *list,
+                             unsigned int *count) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < In;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = row_ptr[r], e = row_ptr[r + 1];
-        if (s < 0 || s >= e || e > nnz || e - s > Lseq) continue;
+        if (Lseq <= 0 || s < 0 || s >= e || e > nnz) continue;
+        if (e - s > Lseq && Lhead <= 0) continue;
         if (s / W == (e - 1) / W) continue;  // inside one tile: the tile kernel runs it
         list[atomicAdd(count, 1u)] = (int32_t)r;
     }
@@ -499,7 +498,7 @@ cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int 
     int64_t blocks = (In + 255) / 256;
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
     if (blocks < 1) blocks = 1;
-    k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.a.nnz, g.chains,
+    k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.Lhead, g.a.nnz, g.chains,
                                                g.nchains);
     *launches += 1;
     return cudaGetLastError();
@@ -519,8 +518,8 @@ static void dispatch_nb(int N, F &&f) {
 }
 
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, int J, int R, const SliceStreams &ss_in, int sms,
-                                 int64_t *launches) {
+                                 bool subslices, float *maps, int J, int R,
+                                 const SliceStreams &ss_in, int sms, int64_t *launches) {
     SliceStreams ss = ss_in;
     const cudaStream_t st = ss.tiles;
     const bool fork = ss.fork && ss.chains_done && ss.maps_done && ss.chains && ss.maps &&
@@ -537,6 +536,8 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     g.row_ptr = row_ptr;
     g.W = W;
     g.Lseq = Lseq;
+    g.Lhead = subslices ? 0 : Lseq;
+    g.subslices = subslices ? 1 : 0;
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     const bool with_maps = maps != nullptr;
@@ -562,7 +563,7 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
         cudaStreamWaitEvent(st, ss.chains_done, 0);
         cudaStreamWaitEvent(st, ss.maps_done, 0);
     }
-    if (with_maps && g.ntiles > 1) {
+    if (with_maps && !subslices && g.ntiles > 1) {
         cudaError_t e = launch_slice_combine(g, J, R, st, sms);
         *launches += 2;
         if (e != cudaSuccess) return e;

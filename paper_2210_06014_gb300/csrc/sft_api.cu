@@ -44,6 +44,7 @@ struct sft_ctx {
     int64_t slice_lseq_mode[kMaxOrder] = {};  // per-mode choice of sft_autotune_slices (0 = none)
     int tensor_cores = 1;  // tcgen05 refresh / core gradient for bfloat16 cached products
     uint64_t tc_wait_ns = 2000000000ull;  // limit of the tensor-core kernels' waits
+    int long_slices = SFT_LONG_MAPS;      // how the slice factor pass runs long slices
     std::string last_error;
 };
 
@@ -489,17 +490,21 @@ static int64_t slice_core_W(const sft_ctx *c, int64_t nnz) {
     return c->slice_tile > 0 ? c->slice_tile : slice_core_tile_length(nnz, c->sms);
 }
 
-// Longest crossing slice run as one element-by-element chain.  A chain step
-// is a dependent sequence of shuffles and FMAs (a few hundred cycles), so
-// chains much longer than a couple of tiles become the pass's tail; measured
-// on the ratings workload, 2 tiles beat both longer chains and maps only.
+// Chain length of the slice factor pass: a crossing slice of at most Lseq
+// nonzeros is run whole as one element-by-element chain, a longer one runs its
+// first Lseq nonzeros as a chain and the rest through composed maps.  Lseq is
+// 0 (every crossing slice through maps) or at least one tile (so that a tile
+// holds at most one map piece per slot).  The default, 2 tiles, is replaced per
+// mode by sft_autotune_slices.
 static int64_t slice_Lseq(const sft_ctx *c, int mode, int64_t W, int64_t nnz) {
     (void)nnz;
     const int64_t tuned = c->slice_lseq_mode[mode];
-    if (tuned != 0) return tuned < 0 ? 0 : tuned;
-    if (c->slice_max_direct > 0) return c->slice_max_direct;
-    if (c->slice_max_direct < 0) return 0;
-    return 2 * W;
+    int64_t L;
+    if (tuned != 0) L = tuned < 0 ? 0 : tuned;
+    else if (c->slice_max_direct > 0) L = c->slice_max_direct;
+    else if (c->slice_max_direct < 0) L = 0;
+    else L = 2 * W;
+    return L > 0 && L < W ? W : L;
 }
 
 size_t sft_slices_scratch_bytes(int64_t nnz) {
@@ -560,7 +565,8 @@ sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *co
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
-    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, mode, W, nnz), (float *)workspace,
+    cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, mode, W, nnz),
+                                         c->long_slices == SFT_LONG_SUBSLICES, (float *)workspace,
                                          c->J[mode], c->R, ss, c->sms, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
     return SFT_OK;
@@ -644,7 +650,8 @@ sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *co
     PassArgs a = pass_args(c, mode, sidx, sval, nullptr, nnz, lr, lambda);
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
-    cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, mode, W, nnz), (float *)workspace,
+    cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, mode, W, nnz),
+                                         c->long_slices == SFT_LONG_SUBSLICES, (float *)workspace,
                                          fid, fcoord, nfibers, V, c->J[mode], c->R, ss, c->sms,
                                          &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "fiber factor launch");
@@ -693,6 +700,14 @@ sft_status sft_set_tensor_cores(sft_ctx *c, int32_t enable) {
     return SFT_OK;
 }
 
+sft_status sft_set_long_slices(sft_ctx *c, int32_t how) {
+    if (!c) return SFT_EINVAL;
+    if (how != SFT_LONG_MAPS && how != SFT_LONG_SUBSLICES)
+        return fail(c, SFT_EINVAL, "long-slice mode must be SFT_LONG_MAPS or SFT_LONG_SUBSLICES");
+    c->long_slices = how;
+    return SFT_OK;
+}
+
 sft_status sft_set_tc_wait_limit(sft_ctx *c, int64_t limit_ns) {
     if (!c) return SFT_EINVAL;
     if (limit_ns < 0 || limit_ns > 60000000000LL)
@@ -716,12 +731,13 @@ sft_status sft_autotune_slices(sft_ctx *c, int32_t mode, const int32_t *const *s
     if (nnz == 0) return SFT_OK;
     const bool fibers = fid != nullptr;
     const int64_t W = slice_W(c, nnz);
-    // candidate limits on the length of a slice run whole (a chain): the
-    // default 2W, powers of two up to 16384, and every crossing slice
-    int64_t cands[10];
+    // candidate chain lengths (a slice up to it runs whole, a longer one runs
+    // that many positions as its head): the default 2W, powers of two up to
+    // 65536, and every crossing slice whole
+    int64_t cands[16];
     int nc = 0;
     cands[nc++] = 2 * W;
-    for (int64_t L = 1024; L <= 16384; L *= 2)
+    for (int64_t L = 1024; L <= 65536; L *= 2)
         if (L > 2 * W) cands[nc++] = L;
     cands[nc++] = (int64_t)1 << 40;
     cudaEvent_t t0, t1;

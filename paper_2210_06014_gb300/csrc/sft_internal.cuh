@@ -89,7 +89,7 @@ cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, floa
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches);
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, int J, int R, const SliceStreams &ss, int sms,
+                                 bool subslices, float *maps, int J, int R, const SliceStreams &ss, int sms,
                                  int64_t *launches);
 cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
                                float *partials, int max_blocks, cudaStream_t st, int sms,
@@ -104,7 +104,7 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
                                 void *scratch, int64_t *nfibers, cudaStream_t st, int sms,
                                 int64_t *launches);
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 float *maps, const int32_t *fid, const int32_t *const *fcoord,
+                                 bool subslices, float *maps, const int32_t *fid, const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss,
                                  int sms, int64_t *launches);
 cudaError_t launch_core_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W,

@@ -128,11 +128,39 @@ __device__ __forceinline__ void walk(const PassArgs &a, int64_t s0, int64_t s1, 
     }
 }
 
+// ---------------------------------------------------------------------------- cp.async
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (BYTES >= 16) {
+#pragma unroll
+        for (int q = 0; q < BYTES / 16; ++q)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * q),
+                         "l"(static_cast<const char *>(src) + 16 * q)
+                         : "memory");
+    } else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+
 struct SliceArgs {
     PassArgs a;              // idx / val in slice order, perm unused
     const int32_t *row_ptr;  // I_n + 1 slice starts
     int64_t W;               // tile length
-    int64_t Lseq;            // crossing slices longer than this are split into maps
+    int64_t Lseq;            // 0, or >= W: crossing slices up to this length run whole as
+                             // one chain; longer ones are long slices
+    int64_t Lhead;           // head of a long slice run as a chain before its map region
+                             // (= Lseq for the exact maps; 0 for sub-slices)
+    int subslices;           // long slices as concurrent sub-slices (no maps)
     int64_t ntiles;
     float *maps;             // [ntiles][2][J*J + J]
     // crossing slices of at most Lseq nonzeros (built per pass by k_chain_list)
@@ -236,15 +264,135 @@ __device__ __forceinline__ void walk_v(const SliceArgs &g, int64_t s0, int64_t s
     }
 }
 
+// Deep shared-memory prefetch ring of the element-by-element walks over the
+// fiber table (tiles and chains).  A chain step depends on the previous one
+// only through the row, and every input of a position (fiber id, value, own
+// coordinate, v) is known in advance, so a chain runs as fast as its
+// arithmetic once the inputs are staged far enough ahead of use: P positions
+// of v (one lane copies its J/T floats of each) and 2P positions of the
+// scalars (lane 0 copies the fiber id, the value and, with WITH_ROW, the
+// coordinate of mode n), all with cp.async, one commit group per step.  The v
+// copy of position q needs its fiber id, which was copied P steps earlier.
+// Per lane group: (P+1) * J floats of v slots and 3 (2P+1) words of scalar
+// slots.  A slot is refilled one step after it was read (its readers have
+// passed the __syncwarp at the top of the next step).
+template <int J, int P>
+struct DeepRing {
+    static constexpr int DV = P + 1;      // v slots
+    static constexpr int DS = 2 * P + 1;  // scalar slots
+    // 4-byte words per lane group, rounded up to 16 bytes so that every
+    // group's ring (and so every v slot) starts 16-byte aligned
+    static constexpr int words = (DV * J + 3 * DS + 3) / 4 * 4;
+};
+
+constexpr int kDeepP = 16;  // prefetch distance (positions) of the deep walk
+
+template <int R, int J, int P, bool WITH_ROW, typename Body>
+__device__ __forceinline__ void walk_v_deep(const SliceArgs &g, float *ring, int64_t s0,
+                                            int64_t s1, int sub, unsigned m, Body &&body) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int DV = DeepRing<J, P>::DV;
+    constexpr int DS = DeepRing<J, P>::DS;
+    const PassArgs &a = g.a;
+    float *vr = ring;                                             // [DV][J]
+    int32_t *fr = reinterpret_cast<int32_t *>(ring + DV * J);     // [DS] fiber ids
+    float *xr = ring + DV * J + DS;                               // [DS] values
+    int32_t *rr = reinterpret_cast<int32_t *>(ring + DV * J + 2 * DS);  // [DS] coordinates
+    const int64_t n = s1 - s0;
+    auto scalars = [&](int64_t q, int slot) {  // lane 0: position q into scalar slot
+        if (sub == 0 && q < n) {
+            cp_async<4>(fr + slot, g.fid + s0 + q);
+            cp_async<4>(xr + slot, a.val + s0 + q);
+            if constexpr (WITH_ROW) cp_async<4>(rr + slot, a.idx[a.n] + s0 + q);
+        }
+    };
+    auto vcopy = [&](int64_t q, int fslot, int vslot) {  // every lane: its part of v of q
+        if (q < n) {
+            const int32_t f = fr[fslot];
+            if ((uint64_t)(int64_t)f < (uint64_t)g.nfibers)
+                cp_async<JL * 4>(vr + vslot * J + sub * JL, g.V + (int64_t)f * J + sub * JL);
+        }
+    };
+    // prologue: scalars of 0 .. P-1 (landed before anything else), then the v
+    // of 0 .. P-1 and the scalars of P .. 2P-1, one commit group per position
+    for (int q = 0; q < P; ++q) scalars(q, q);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp(m);
+    for (int q = 0; q < P; ++q) {
+        vcopy(q, q, q);
+        scalars(q + P, q + P);
+        cp_async_commit();
+    }
+    int vs = 0;       // v slot of position i
+    int ss = 0;       // scalar slot of position i
+    int fs = P;       // scalar slot of position i + P
+    int row_pf = -1;  // last coordinate whose factor row was prefetched
+    for (int64_t i = 0; i < n; ++i) {
+        cp_async_wait<P - 1>();  // this lane's copies of step i - P have landed
+        __syncwarp(m);           // ... and lane 0's scalars; slots of i - 1 are free
+        const int32_t f = fr[ss];
+        const float x = xr[ss];
+        int32_t row = WITH_ROW ? rr[ss] : -1;
+        float vq[JL];
+        const float *src = vr + vs * J + sub * JL;
+        if constexpr (JL >= 4) {
+#pragma unroll
+            for (int q = 0; q < JL; q += 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
+                vq[q] = t4.x; vq[q + 1] = t4.y; vq[q + 2] = t4.z; vq[q + 3] = t4.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < JL; ++q) vq[q] = src[q];
+        }
+        if constexpr (WITH_ROW) {
+            // a coordinate P positions ahead that starts a new slice: bring its
+            // factor row towards the SM (L2) before the walk switches to it
+            const int32_t rn = rr[fs];
+            if (sub == 0 && i + P < n && rn != row_pf && (uint32_t)rn < (uint32_t)a.dims[a.n]) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.A + (int64_t)rn * J));
+                row_pf = rn;
+            }
+        }
+        const int prev_vs = vs == 0 ? DV - 1 : vs - 1;  // slot of i - 1 == slot of i + P
+        const int prev_ss = ss == 0 ? DS - 1 : ss - 1;  // slot of i - 1 == slot of i + 2P
+        vcopy(i + P, fs, prev_vs);
+        scalars(i + 2 * P, prev_ss);
+        cp_async_commit();
+        bool bad = (uint64_t)(int64_t)f >= (uint64_t)g.nfibers;
+        if (WITH_ROW && (uint32_t)row >= (uint32_t)a.dims[a.n]) {
+            bad = true;
+            row = -1;
+        }
+        if (bad && sub == 0) atomicOr(a.err, kErrIndex);
+        if (bad) {
+#pragma unroll
+            for (int q = 0; q < JL; ++q) vq[q] = 0.f;
+        }
+        body(row, x, !bad, vq);
+        vs = vs + 1 == DV ? 0 : vs + 1;
+        ss = ss + 1 == DS ? 0 : ss + 1;
+        fs = fs + 1 == DS ? 0 : fs + 1;
+    }
+    cp_async_wait<0>();
+    __syncwarp(m);
+}
+
 // Calls step(row, x, ok, vq) for positions [s0, s1) in order, where vq is the
 // lane's J/T entries of v: computed from the gathered rows (FV = false) or
 // read from the per-fiber table (FV = true).
 template <bool FV, int NB, int R, int J, typename CT, int DMAX, bool WITH_ROW, typename Step>
 __device__ __forceinline__ void walk_steps(const SliceArgs &g, const float *sB, int64_t s0,
-                                           int64_t s1, int sub, unsigned m, Step &&step) {
+                                           int64_t s1, int sub, unsigned m, Step &&step,
+                                           float *deep = nullptr) {
     constexpr int JL = J / (R / 4);
     if constexpr (FV) {
-        walk_v<R, J, DMAX, WITH_ROW>(g, s0, s1, sub, step);
+        if (deep)
+            walk_v_deep<R, J, kDeepP, WITH_ROW>(g, deep, s0, s1, sub, m, step);
+        else
+            walk_v<R, J, DMAX, WITH_ROW>(g, s0, s1, sub, step);
     } else {
         walk<NB, R, CT, DMAX, WITH_ROW>(g.a, s0, s1, sub,
                                         [&](int32_t row, float x, bool ok, const float4 &p) {
@@ -280,7 +428,8 @@ __device__ __forceinline__ void store_run(float *p, const float (&r)[L]) {
 // cached rows are loaded while the current one is computed.
 template <bool FV, int NB, int R, int J, typename CT>
 __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, int32_t r,
-                                           int64_t s0, int64_t s1, int sub, unsigned m) {
+                                           int64_t s0, int64_t s1, int sub, unsigned m,
+                                           float *deep) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
     const PassArgs &a = g.a;
@@ -311,7 +460,7 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
         xq = x;
         okq = ok;
         have = true;
-    });
+    }, deep);
     if (have) apply();
     store_run<JL>(arow, av);
 }
@@ -340,11 +489,20 @@ constexpr int kSliceThreads = 256;
 // tile's first run if its slice started before the tile and its last run if
 // its slice continues after it; the factor row is switched in place whenever
 // the slice changes.
+// Dynamic shared memory of the direct kernels in the fiber variant: one deep
+// prefetch ring per lane group (none in the per-nonzero variant).
+template <bool FV, int R, int J>
+constexpr size_t direct_smem() {
+    return FV ? (size_t)(kSliceThreads / (R / 4)) * DeepRing<J, kDeepP>::words * 4 : 0;
+}
+
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles(SliceArgs g) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
     __shared__ __align__(16) float sB[J * R];
+    extern __shared__ __align__(16) float dyn_ring[];
+    float *deep = FV ? dyn_ring + (threadIdx.x / T) * DeepRing<J, kDeepP>::words : nullptr;
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
     __syncthreads();
     const PassArgs &a = g.a;
@@ -397,18 +555,21 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
 #pragma unroll
                 for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
             }
-        });
+        }, deep);
         if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
     }
 }
 
-// Crossing slices of at most Lseq nonzeros, whole, one per lane group: the
-// groups take the slices of the pass's chain list in turn, so every group of
-// every warp has work while the list lasts.
+// Crossing slices, one per lane group: a slice of at most Lseq nonzeros is
+// run whole, a longer one its first Lseq nonzeros (its head); the groups take
+// the slices of the pass's chain list in turn, so every group of every warp
+// has work while the list lasts.
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chains(SliceArgs g) {
     constexpr int T = R / 4;
     __shared__ __align__(16) float sB[J * R];
+    extern __shared__ __align__(16) float dyn_ring[];
+    float *deep = FV ? dyn_ring + (threadIdx.x / T) * DeepRing<J, kDeepP>::words : nullptr;
     for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -416,13 +577,18 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_chain
     const unsigned m = group_mask<T>(lane);
     const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
     const int64_t n = (int64_t)*g.nchains;
-    for (int64_t c = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T; c < n;
-         c += groups) {
+    // entry c goes to block c % gridDim.x: a short list spreads over every SM
+    // instead of filling the first blocks (a chain is a dependent sequence, so
+    // chains sharing an SM share its issue slots)
+    for (int64_t c = (int64_t)(threadIdx.x / T) * gridDim.x + blockIdx.x; c < n; c += groups) {
         const int32_t r = __ldg(g.chains + c);
         if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) continue;
         const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
         if (!slice_ok(g, s, e)) continue;
-        run_direct<FV, NB, R, J, CT>(g, sB, r, s, e, sub, m);
+        // a slice of at most Lseq nonzeros whole; a longer one its first Lseq
+        // (the rest goes through maps, applied to the row this leaves)
+        run_direct<FV, NB, R, J, CT>(g, sB, r, s, e - s <= g.Lseq ? e : min(e, s + g.Lhead), sub,
+                                     m, deep);
     }
 }
 
@@ -441,29 +607,6 @@ struct MapRing {
     static constexpr int D = GPB * DMAX * J * 4 <= 32768 ? DMAX : 2;
     static constexpr bool use = GPB * D * J * 4 <= 32768;  // else the register walk
 };
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async(float *dst, const float *src) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    if constexpr (BYTES >= 16) {
-#pragma unroll
-        for (int q = 0; q < BYTES / 16; ++q)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * q),
-                         "l"(src + 4 * q)
-                         : "memory");
-    } else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES)
-                     : "memory");
-}
 
 // Calls step(v, vl, x, ok) for slice positions [s0, s1) in order: v = all J
 // entries of the position's fiber v (shared memory), vl = the lane's J/T.
@@ -680,9 +823,45 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
     store_run<JL>(out + J * J + sub * JL, cv);
 }
 
-// One group per tile: maps for the tile's first run (if its slice started
-// before the tile) and last run (if its slice continues after the tile) when
-// that slice is longer than Lseq.
+// The map piece of tile t on `side` (slot).  A crossing slice longer than
+// Lseq (a long slice) runs its first Lhead positions as a chain (k_slices_chains)
+// and its map region [hs, e), hs = s + Lhead, through composed affine maps, one
+// piece per tile the region touches:
+//   slot 0: the region started before the tile: piece [p0, min(e, p1));
+//   slot 1: the region starts inside the tile: piece [hs, min(e, p1)).
+// With Lhead >= W only the slice holding the tile's first position p0 can have
+// a piece in the tile (a slice starting inside the tile has its region start
+// at least W later).  With Lhead = 0 the slot-1 piece belongs to the slice
+// holding the last position p1 - 1.  Lhead is 0 or at least W (the callers
+// enforce it), so the two slots never clash.
+__device__ __forceinline__ bool map_piece(const SliceArgs &g, int64_t t, int side, int32_t &r,
+                                          int64_t &s, int64_t &e, int64_t &hs, int64_t &q0,
+                                          int64_t &q1) {
+    const int64_t p0 = t * g.W;
+    const int64_t p1 = min(g.a.nnz, p0 + g.W);
+    const int64_t at = (side == 0 || g.Lhead > 0) ? p0 : p1 - 1;
+    r = __ldg(g.a.idx[g.a.n] + at);
+    if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) return false;
+    s = __ldg(g.row_ptr + r);
+    e = __ldg(g.row_ptr + r + 1);
+    if (!slice_ok(g, s, e) || at < s || at >= e) {
+        atomicOr(g.a.err, kErrIndex);
+        return false;
+    }
+    if (e - s <= g.Lseq || (s >= p0 && e <= p1)) return false;  // not long / not crossing
+    hs = s + g.Lhead;
+    if (side == 0) {
+        if (hs >= p0) return false;
+        q0 = p0;
+    } else {
+        if (hs < p0 || hs >= p1 || hs >= e) return false;
+        q0 = hs;
+    }
+    q1 = min(e, p1);
+    return true;
+}
+
+// One group per tile: the tile's map pieces (at most one per slot).
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
@@ -698,30 +877,71 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
     const unsigned m = group_mask<T>(lane);
     float *ring = RINGED ? sring + (threadIdx.x / T) * (MapRing<R, J>::D * J) : nullptr;
     const int64_t groups = (int64_t)gridDim.x * GPB;
-    const int32_t *rowidx = g.a.idx[g.a.n];
     for (int64_t t = (int64_t)blockIdx.x * GPB + threadIdx.x / T; t < g.ntiles;
          t += groups) {
-        const int64_t p0 = t * g.W;
-        const int64_t p1 = min(g.a.nnz, p0 + g.W);
         for (int side = 0; side < 2; ++side) {
-            const int64_t at = side == 0 ? p0 : p1 - 1;
-            const int32_t r = __ldg(rowidx + at);
-            if ((uint32_t)r >= (uint32_t)g.a.dims[g.a.n]) continue;
-            const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
-            if (!slice_ok(g, s, e) || at < s || at >= e) {
-                atomicOr(g.a.err, kErrIndex);
-                continue;
-            }
-            if (e - s <= g.Lseq) continue;
-            const bool before = s < p0, after = e > p1;
-            // slot 0: run that started before the tile; slot 1: run that starts in
-            // the tile and continues after it
-            if (side == 0 && before) {
-                compose_map<FV, NB, R, J, CT>(g, sB, ring, p0, min(e, p1), sub, m,
-                                      g.maps + (t * 2 + 0) * (int64_t)(J * J + J));
-            } else if (side == 1 && after && !before) {
-                compose_map<FV, NB, R, J, CT>(g, sB, ring, max(s, p0), p1, sub, m,
-                                      g.maps + (t * 2 + 1) * (int64_t)(J * J + J));
+            int32_t r;
+            int64_t s, e, hs, q0, q1;
+            if (!map_piece(g, t, side, r, s, e, hs, q0, q1)) continue;
+            compose_map<FV, NB, R, J, CT>(g, sB, ring, q0, q1, sub, m,
+                                          g.maps + (t * 2 + side) * (int64_t)(J * J + J));
+        }
+    }
+}
+
+// Long slices in the paper's B-CSF manner (Section "Tensor Storage Format":
+// heavy slices cut into sub-slices that are walked concurrently), used instead
+// of the exact maps when the context asks for sub-slices: every map piece
+// (here a sub-slice of at most W nonzeros) is walked element by element from
+// the row as it stands in memory when the walk starts, and its change to the
+// row is added back with vector atomics.  Sub-slices of one row overlap in
+// time, so the result depends on scheduling (Hogwild within a row); it is
+// checked by the per-epoch RMSE only.
+template <bool FV, int NB, int R, int J, typename CT>
+__global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_subs(SliceArgs g) {
+    constexpr int T = R / 4;
+    constexpr int JL = J / T;
+    constexpr int GPB = kSliceThreads / T;
+    __shared__ __align__(16) float sB[J * R];
+    extern __shared__ __align__(16) float dyn_ring[];
+    float *deep = FV ? dyn_ring + (threadIdx.x / T) * DeepRing<J, kDeepP>::words : nullptr;
+    for (int q = threadIdx.x; q < J * R; q += blockDim.x) sB[q] = g.a.B[q];
+    __syncthreads();
+    const PassArgs &a = g.a;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);
+    const unsigned m = group_mask<T>(lane);
+    const int64_t groups = (int64_t)gridDim.x * GPB;
+    for (int64_t t = (int64_t)blockIdx.x * GPB + threadIdx.x / T; t < g.ntiles; t += groups) {
+        for (int side = 0; side < 2; ++side) {
+            int32_t r;
+            int64_t s, e, hs, q0, q1;
+            if (!map_piece(g, t, side, r, s, e, hs, q0, q1)) continue;
+            float *arow = a.A + (int64_t)r * J + sub * JL;
+            float a0[JL], av[JL];
+#pragma unroll
+            for (int q = 0; q < JL; ++q) av[q] = a0[q] = __ldcg(arow + q);
+            walk_steps<FV, NB, R, J, CT, 4, false>(g, sB, q0, q1, sub, m,
+                                                   [&](int32_t, float x, bool ok,
+                                                       const float (&vq)[JL]) {
+                float dot = 0.f;
+#pragma unroll
+                for (int q = 0; q < JL; ++q) dot = fmaf(av[q], vq[q], dot);
+                const float ev = x - group_sum_m<T>(dot, m);
+                if (ok) {
+#pragma unroll
+                    for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (ev * vq[q] - a.lam * av[q]);
+                }
+            }, deep);
+            if constexpr (JL >= 4) {
+#pragma unroll
+                for (int q = 0; q < JL; q += 4)
+                    atomicAdd(reinterpret_cast<float4 *>(arow + q),
+                              make_float4(av[q] - a0[q], av[q + 1] - a0[q + 1],
+                                          av[q + 2] - a0[q + 2], av[q + 3] - a0[q + 3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < JL; ++q) atomicAdd(arow + q, av[q] - a0[q]);
             }
         }
     }
@@ -838,22 +1058,39 @@ template <bool FV, int NB, int R, int J, typename CT>
 void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss, int sms,
                      int64_t *launches) {
     const int gpb = kSliceThreads / (R / 4);
+    constexpr size_t dsm = direct_smem<FV, R, J>();
+    if (g.subslices && g.ntiles > 1) {
+        if (dsm > 0)
+            cudaFuncSetAttribute(k_slices_subs<FV, NB, R, J, CT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        const int gs = grid_for(k_slices_subs<FV, NB, R, J, CT>, kSliceThreads, dsm, gpb,
+                                g.ntiles, sms);
+        k_slices_subs<FV, NB, R, J, CT><<<gs, kSliceThreads, dsm, ss.maps>>>(g);
+        *launches += 1;
+    }
     // maps first: it is the longest of the three, so its blocks take the SMs first
-    if (with_maps && g.ntiles > 1) {
+    if (with_maps && !g.subslices && g.ntiles > 1) {
         const int gm = grid_for(k_slices_maps<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles,
                                 sms);
         k_slices_maps<FV, NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
         *launches += 1;
     }
+    if (dsm > 0) {
+        cudaFuncSetAttribute(k_slices_chains<FV, NB, R, J, CT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        cudaFuncSetAttribute(k_slices_tiles<FV, NB, R, J, CT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    }
     if (g.ntiles > 1) {
         // the list holds at most one slice per tile boundary
-        const int gch = grid_for(k_slices_chains<FV, NB, R, J, CT>, kSliceThreads, 0, gpb,
+        const int gch = grid_for(k_slices_chains<FV, NB, R, J, CT>, kSliceThreads, dsm, gpb,
                                  g.ntiles - 1, sms);
-        k_slices_chains<FV, NB, R, J, CT><<<gch, kSliceThreads, 0, ss.chains>>>(g);
+        k_slices_chains<FV, NB, R, J, CT><<<gch, kSliceThreads, dsm, ss.chains>>>(g);
         *launches += 1;
     }
-    const int gd = grid_for(k_slices_tiles<FV, NB, R, J, CT>, kSliceThreads, 0, gpb, g.ntiles, sms);
-    k_slices_tiles<FV, NB, R, J, CT><<<gd, kSliceThreads, 0, ss.tiles>>>(g);
+    const int gd = grid_for(k_slices_tiles<FV, NB, R, J, CT>, kSliceThreads, dsm, gpb, g.ntiles,
+                            sms);
+    k_slices_tiles<FV, NB, R, J, CT><<<gd, kSliceThreads, dsm, ss.tiles>>>(g);
     *launches += 1;
 }
 

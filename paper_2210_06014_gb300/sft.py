@@ -37,7 +37,8 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_last_error", "sft_batch_destroy", "sft_batch_plan",
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
             "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers",
-            "sft_autotune_slices", "sft_set_tensor_cores", "sft_set_tc_wait_limit"]
+            "sft_autotune_slices", "sft_set_tensor_cores", "sft_set_tc_wait_limit",
+            "sft_set_long_slices"]
 
 
 class SftError(RuntimeError):
@@ -132,6 +133,8 @@ def load(build_if_missing: bool = True):
     lib.sft_set_tensor_cores.restype = ctypes.c_int
     lib.sft_set_tc_wait_limit.argtypes = [ctx, i64]
     lib.sft_set_tc_wait_limit.restype = ctypes.c_int
+    lib.sft_set_long_slices.argtypes = [ctx, i32]
+    lib.sft_set_long_slices.restype = ctypes.c_int
     lib.sft_update_factors_noalloc.argtypes = [
         i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
         ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
@@ -360,6 +363,14 @@ def sft_set_tensor_cores(ctx, enable: bool = True) -> None:
     _check(lib, ctx, lib.sft_set_tensor_cores(ctx, 1 if enable else 0), "sft_set_tensor_cores")
 
 
+SFT_LONG_MAPS, SFT_LONG_SUBSLICES = 0, 1
+
+
+def sft_set_long_slices(ctx, how: int) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_set_long_slices(ctx, int(how)), "sft_set_long_slices")
+
+
 def sft_set_tc_wait_limit(ctx, limit_ns: int) -> None:
     lib = load()
     _check(lib, ctx, lib.sft_set_tc_wait_limit(ctx, int(limit_ns)), "sft_set_tc_wait_limit")
@@ -559,6 +570,10 @@ class Decomposition:
 
     def set_slice_tiling(self, tile: int = 0, max_direct: int = 0):
         sft_set_slice_tiling(self.ctx, tile, max_direct)
+
+    def set_long_slices(self, how: int):
+        """SFT_LONG_MAPS (exact, default) or SFT_LONG_SUBSLICES (B-CSF style)."""
+        sft_set_long_slices(self.ctx, how)
 
     def update_factors_slices(self, sl: Slices, lr=0.01, lam=0.01):
         need = max(16, sft_slices_workspace_bytes(self.ctx, sl.mode, sl.nnz))
