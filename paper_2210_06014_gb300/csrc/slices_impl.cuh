@@ -78,6 +78,13 @@ __device__ __forceinline__ float4 product(const Rows<NO, CT> &w) {
     return p;
 }
 
+// One entry of the element step a <- a + lr (e v - lambda a) (Eq. (10)),
+// with its roundings spelled out so that every kernel that runs the step
+// (lane groups or one lane per chain) produces the same bits.
+__device__ __forceinline__ float row_step(float a, float e, float v, float lr, float lam) {
+    return __fmaf_rn(lr, __fmaf_rn(-lam, a, __fmul_rn(e, v)), a);
+}
+
 // Prefetch depth of the slice walks: coordinates and cached rows of the next
 // D positions are in flight while the current one is computed.
 template <int NO, int DMAX>
@@ -449,7 +456,7 @@ __device__ __forceinline__ void run_direct(const SliceArgs &g, const float *sB, 
         const float e = xq - group_sum_m<T>(dot, m);
         if (okq) {
 #pragma unroll
-            for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
+            for (int q = 0; q < JL; ++q) av[q] = row_step(av[q], e, vq[q], a.lr, a.lam);
         }
     };
     walk_steps<FV, NB, R, J, CT, 4, false>(g, sB, s0, s1, sub, m,
@@ -553,11 +560,234 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_tiles
             const float e = x - group_sum_m<T>(dot, m);
             if (ok) {
 #pragma unroll
-                for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (e * vq[q] - a.lam * av[q]);
+                for (int q = 0; q < JL; ++q) av[q] = row_step(av[q], e, vq[q], a.lr, a.lam);
             }
         }, deep);
         if (cur >= 0) store_run<JL>(a.A + (int64_t)cur * J + sub * JL, av);
     }
+}
+
+// ============================================================================ factor: one lane per chain
+// In the fiber variant with J_n <= 16 an element-by-element chain (a tile's
+// short slices, a crossing slice run whole, the head of a long slice) is run by
+// one lane holding the whole row: its step (a . v, the residual, the row
+// update) needs no shuffle, and the lane stages its own inputs with cp.async
+// into a private ring (no group synchronisation).  The sum a . v is taken in
+// the order the T = R/4-lane groups of the other kernels take it (sequential
+// over each group lane's J/T entries, then the butterfly of the group sum), so
+// the rows come out bitwise equal to the lane-group kernels and to the
+// per-nonzero path.
+template <int T, int J>
+__device__ __forceinline__ float group_order_dot(const float (&a)[J], const float (&v)[J]) {
+    constexpr int JL = J / T;
+    float p[T];
+#pragma unroll
+    for (int l = 0; l < T; ++l) {
+        float d = 0.f;
+#pragma unroll
+        for (int q = 0; q < JL; ++q) d = fmaf(a[l * JL + q], v[l * JL + q], d);
+        p[l] = d;
+    }
+    // butterfly: at distance w every member adds its partner's value
+#pragma unroll
+    for (int w = T / 2; w >= 1; w >>= 1) {
+        float nxt[T];
+#pragma unroll
+        for (int l = 0; l < T; ++l) nxt[l] = p[l] + p[l ^ w];
+#pragma unroll
+        for (int l = 0; l < T; ++l) p[l] = nxt[l];
+    }
+    return p[0];
+}
+
+// Per-lane ring of the one-lane walks: P positions of v (J floats, plus J
+// floats of the factor row at positions where a new slice starts, for the tile
+// walk) and 2P positions of the scalars (fiber id, value, mode-n coordinate).
+template <int J, int P, bool ROWS>
+struct LaneRing {
+    static constexpr int DV = P + 1;
+    static constexpr int DS = 2 * P + 1;
+    static constexpr int VW = ROWS ? 2 * J : J;  // floats per v slot
+    static constexpr int words = (DV * VW + 3 * DS + 3) / 4 * 4;  // 16-byte multiple
+};
+
+constexpr int kLaneThreads = 64;  // block size of the one-lane kernels
+constexpr int kLaneChainP = 16;   // prefetch distance of a chain
+constexpr int kLaneTileP = 8;     // ... of a tile walk (its slots also hold rows)
+
+// Calls body(row, x, ok, v, newrow) for positions [s0, s1) in order: v = the
+// position's v (J floats); with ROWS, row = its mode-n coordinate and newrow =
+// the pass-start value of that row's factor row (valid where the coordinate
+// differs from the previous position's).
+template <int J, int P, bool ROWS, typename Body>
+__device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64_t s0, int64_t s1,
+                                          Body &&body) {
+    using LR = LaneRing<J, P, ROWS>;
+    constexpr int DV = LR::DV, DS = LR::DS, VW = LR::VW;
+    const PassArgs &a = g.a;
+    float *vr = ring;
+    int32_t *fr = reinterpret_cast<int32_t *>(ring + DV * VW);
+    float *xr = ring + DV * VW + DS;
+    int32_t *rr = reinterpret_cast<int32_t *>(ring + DV * VW + 2 * DS);
+    const int64_t n = s1 - s0;
+    const uint32_t In = (uint32_t)a.dims[a.n];
+    int32_t last_row = -1;  // coordinate of the last position whose v copy was issued
+    auto scalars = [&](int64_t q, int slot) {
+        if (q < n) {
+            cp_async<4>(fr + slot, g.fid + s0 + q);
+            cp_async<4>(xr + slot, a.val + s0 + q);
+            if constexpr (ROWS) cp_async<4>(rr + slot, a.idx[a.n] + s0 + q);
+        }
+    };
+    auto vcopy = [&](int64_t q, int fslot, int vslot) {
+        if (q < n) {
+            const int32_t f = fr[fslot];
+            if ((uint64_t)(int64_t)f < (uint64_t)g.nfibers)
+                cp_async<J * 4>(vr + vslot * VW, g.V + (int64_t)f * J);
+            if constexpr (ROWS) {
+                const int32_t r = rr[fslot];
+                if (r != last_row && (uint32_t)r < In)
+                    cp_async<J * 4>(vr + vslot * VW + J, a.A + (int64_t)r * J);
+                last_row = r;
+            }
+        }
+    };
+    for (int q = 0; q < P; ++q) scalars(q, q);
+    cp_async_commit();
+    cp_async_wait<0>();
+    for (int q = 0; q < P; ++q) {
+        vcopy(q, q, q);
+        scalars(q + P, q + P);
+        cp_async_commit();
+    }
+    int vs = 0, ss = 0, fs = P;
+    for (int64_t i = 0; i < n; ++i) {
+        cp_async_wait<P - 1>();  // this lane's copies of step i - P have landed
+        const int32_t f = fr[ss];
+        const float x = xr[ss];
+        int32_t row = ROWS ? rr[ss] : -1;
+        float v[J];
+        const float *src = vr + vs * VW;
+#pragma unroll
+        for (int q = 0; q < J; q += 4) {
+            const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
+            v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
+        }
+        bool ok = (uint64_t)(int64_t)f < (uint64_t)g.nfibers;
+        if (ROWS && (uint32_t)row >= In) {
+            ok = false;
+            row = -1;
+        }
+        if (!ok) atomicOr(a.err, kErrIndex);
+        body(row, x, ok, v, src + J);  // reads the slot before it is refilled below
+        const int prev_vs = vs == 0 ? DV - 1 : vs - 1;
+        const int prev_ss = ss == 0 ? DS - 1 : ss - 1;
+        vcopy(i + P, fs, prev_vs);
+        scalars(i + 2 * P, prev_ss);
+        cp_async_commit();
+        vs = vs + 1 == DV ? 0 : vs + 1;
+        ss = ss + 1 == DS ? 0 : ss + 1;
+        fs = fs + 1 == DS ? 0 : fs + 1;
+    }
+    cp_async_wait<0>();
+}
+
+// One element step on a whole row held by one lane: the same operations as
+// the lane-group kernels (sum order of a T-lane group, then
+// a += lr (e v - lambda a)).
+template <int T, int J>
+__device__ __forceinline__ void lane_step(const PassArgs &a, float (&av)[J], const float (&v)[J],
+                                          float x, bool ok) {
+    const float e = x - group_order_dot<T, J>(av, v);
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < J; ++q) av[q] = row_step(av[q], e, v[q], a.lr, a.lam);
+    }
+}
+
+// Crossing slices (whole, or the head of a long slice), one per lane; list
+// entry c goes to block c % gridDim.x so that a short list spreads over the SMs.
+template <int R, int J>
+__global__ void __launch_bounds__(kLaneThreads) k_slices_chains1(SliceArgs g) {
+    constexpr int T = R / 4;
+    using LR = LaneRing<J, kLaneChainP, false>;
+    extern __shared__ __align__(16) float lane_ring[];
+    float *ring = lane_ring + threadIdx.x * LR::words;
+    const PassArgs &a = g.a;
+    const int64_t n = (int64_t)*g.nchains;
+    const int64_t lanes = (int64_t)gridDim.x * kLaneThreads;
+    for (int64_t c = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; c < n; c += lanes) {
+        const int32_t r = __ldg(g.chains + c);
+        if ((uint32_t)r >= (uint32_t)a.dims[a.n]) continue;
+        const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+        if (!slice_ok(g, s, e)) continue;
+        const int64_t e1 = e - s <= g.Lseq ? e : min(e, s + g.Lhead);
+        float *arow = a.A + (int64_t)r * J;
+        float av[J];
+        load_run<J>(arow, av);
+        walk_lane<J, kLaneChainP, false>(g, ring, s, e1,
+                                         [&](int32_t, float x, bool ok, const float (&v)[J],
+                                             const float *) { lane_step<T, J>(a, av, v, x, ok); });
+        store_run<J>(arow, av);
+    }
+}
+
+// Slices inside tiles, one tile per lane (the same bounds as k_slices_tiles);
+// the factor row of each new slice is staged in the ring with the position that
+// starts it.
+template <int R, int J>
+__global__ void __launch_bounds__(kLaneThreads) k_slices_tiles1(SliceArgs g) {
+    constexpr int T = R / 4;
+    using LR = LaneRing<J, kLaneTileP, true>;
+    extern __shared__ __align__(16) float lane_ring[];
+    float *ring = lane_ring + threadIdx.x * LR::words;
+    const PassArgs &a = g.a;
+    const int64_t lanes = (int64_t)gridDim.x * kLaneThreads;
+    const int32_t *rowidx = a.idx[a.n];
+    const uint32_t In = (uint32_t)a.dims[a.n];
+    for (int64_t t = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x; t < g.ntiles; t += lanes) {
+        const int64_t p0 = t * g.W;
+        const int64_t p1 = min(a.nnz, p0 + g.W);
+        int64_t q0 = p0, q1 = p1;
+        bool bad = false;
+        const int32_t r0 = __ldg(rowidx + p0);
+        if (p0 > 0 && (uint32_t)r0 < In && __ldg(rowidx + p0 - 1) == r0) {
+            const int64_t e0 = __ldg(g.row_ptr + r0 + 1);
+            if (e0 <= p0 || e0 > a.nnz) bad = true;
+            else q0 = min(e0, p1);
+        }
+        const int32_t r1 = __ldg(rowidx + p1 - 1);
+        if (p1 < a.nnz && (uint32_t)r1 < In && __ldg(rowidx + p1) == r1) {
+            const int64_t s1 = __ldg(g.row_ptr + r1);
+            if (s1 < 0 || s1 > p1 - 1) bad = true;
+            else q1 = max(s1, q0);
+        }
+        if (bad) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        if (q0 >= q1) continue;
+        int32_t cur = -1;
+        float av[J];
+#pragma unroll
+        for (int q = 0; q < J; ++q) av[q] = 0.f;
+        walk_lane<J, kLaneTileP, true>(g, ring, q0, q1,
+                                       [&](int32_t row, float x, bool ok, const float (&v)[J],
+                                           const float *newrow) {
+            if (row != cur) {  // the slice changes: write the finished row, take the next
+                if (cur >= 0) store_run<J>(a.A + (int64_t)cur * J, av);
+                cur = row;
+                if (cur >= 0) load_run<J>(newrow, av);
+            }
+            lane_step<T, J>(a, av, v, x, ok);
+        });
+        if (cur >= 0) store_run<J>(a.A + (int64_t)cur * J, av);
+    }
+}
+
+template <int R, int J>
+constexpr bool lane_kernels() {
+    return J <= 16;
 }
 
 // Crossing slices, one per lane group: a slice of at most Lseq nonzeros is
@@ -930,7 +1160,7 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_DIRECT_MINB) k_slices_subs(
                 const float ev = x - group_sum_m<T>(dot, m);
                 if (ok) {
 #pragma unroll
-                    for (int q = 0; q < JL; ++q) av[q] = av[q] + a.lr * (ev * vq[q] - a.lam * av[q]);
+                    for (int q = 0; q < JL; ++q) av[q] = row_step(av[q], ev, vq[q], a.lr, a.lam);
                 }
             }, deep);
             if constexpr (JL >= 4) {
@@ -1074,6 +1304,25 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
                                 sms);
         k_slices_maps<FV, NB, R, J, CT><<<gm, kSliceThreads, 0, ss.maps>>>(g);
         *launches += 1;
+    }
+    if constexpr (FV && lane_kernels<R, J>()) {
+        constexpr size_t csm = (size_t)kLaneThreads * LaneRing<J, kLaneChainP, false>::words * 4;
+        constexpr size_t tsm = (size_t)kLaneThreads * LaneRing<J, kLaneTileP, true>::words * 4;
+        cudaFuncSetAttribute(k_slices_chains1<R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)csm);
+        cudaFuncSetAttribute(k_slices_tiles1<R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tsm);
+        if (g.ntiles > 1) {
+            const int gch = grid_for(k_slices_chains1<R, J>, kLaneThreads, csm, kLaneThreads,
+                                     g.ntiles - 1, sms);
+            k_slices_chains1<R, J><<<gch, kLaneThreads, csm, ss.chains>>>(g);
+            *launches += 1;
+        }
+        const int gd = grid_for(k_slices_tiles1<R, J>, kLaneThreads, tsm, kLaneThreads, g.ntiles,
+                                sms);
+        k_slices_tiles1<R, J><<<gd, kLaneThreads, tsm, ss.tiles>>>(g);
+        *launches += 1;
+        return;
     }
     if (dsm > 0) {
         cudaFuncSetAttribute(k_slices_chains<FV, NB, R, J, CT>,
