@@ -74,6 +74,13 @@ def parse():
     p.add_argument("--no-e2e-raw", action="store_true",
                    help="skip the end-to-end figure that rebuilds the slice layouts and fiber "
                         "tables from raw COO every step")
+    p.add_argument("--order", default="storage", choices=["csf", "storage"],
+                   help="visit order of the nonzeros inside each slice: the paper's B-CSF "
+                        "traversal (sorted by the other modes' coordinates) or storage order")
+    p.add_argument("--blocked-chains", default="on", choices=["on", "off"],
+                   help="chains of 256+ nonzeros of the fiber pass in 32-position blocks "
+                        "(Gram matrix on the tensor cores + triangular solve) or element by "
+                        "element")
     p.add_argument("--long-slices", default="maps", choices=["maps", "subslices"],
                    help="long slices exactly through composed maps (Algorithm 4 order), or as "
                         "concurrent sub-slices merged with atomic adds (the paper's B-CSF manner)")
@@ -274,19 +281,24 @@ def cpu_oracle_grad_rate(T, sample: int):
     return S / dt, dt, S
 
 
-def cpu_oracle_epoch_rate(T, sample: int):
+def cpu_oracle_epoch_rate(T, sample: int, order: str = "storage"):
     """Oracle (FP64, single thread) on the first `sample` training nonzeros with
-    the same schedule (factor rows element by element, core once per pass);
-    returns (nonzeros per second, seconds, sample)."""
+    the same schedule (factor rows element by element in the same visit order,
+    core once per pass); returns (nonzeros per second, seconds, sample)."""
     import numpy as np
     import oracle
+    from paper_2210_06014_gb300 import synth
     oracle.build()
     S = min(sample, T.nnz)
     idx = [i[:S].cpu().numpy() for i in T.idx]
     val = T.val[:S].cpu().numpy()
+    pf = None
+    if order == "csf":
+        tix = [i[:S].cpu() for i in T.idx]
+        pf = [synth.csf_order(tix, n).numpy().astype(np.uint32) for n in range(len(idx))]
     m = oracle.Model([a.cpu().numpy() for a in T.A0], [b.cpu().numpy() for b in T.B0])
     t0 = time.perf_counter()
-    m.epoch(idx, val, None, None, batch_factor=1, batch_core=S)
+    m.epoch(idx, val, pf, None, batch_factor=1, batch_core=S)
     dt = time.perf_counter() - t0
     return S / dt, dt, S
 
@@ -689,7 +701,8 @@ def main():
             if args.workload == "autograd":
                 rate, dt, S = cpu_oracle_grad_rate(T, max(10_000, args.cpu_sample // 4))
             else:
-                rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4))
+                rate, dt, S = cpu_oracle_epoch_rate(T, max(10_000, args.cpu_sample // 4),
+                                                    args.order)
             if i >= args.warmup:
                 steps.append((rate, dt))
         rate = statistics.median(r for r, _ in steps)
@@ -728,6 +741,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     """One step = one epoch of Algorithm 2 on tensor T (factor pass + refresh per
     mode, then core pass + refresh per mode, then the test-set residual sums).
     Returns the JSON line (rank 0)."""
+    from paper_2210_06014_gb300 import synth
     dev = T.val.device
     workload = spec.name
     N, J, R = spec.order, spec.J[0], spec.R
@@ -748,9 +762,13 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         dec.set_slice_tiling(args.slice_tile, args.slice_max_direct)
         if args.long_slices == "subslices":
             dec.set_long_slices(sft.SFT_LONG_SUBSLICES)
+        dec.set_blocked_chains(args.blocked_chains == "on")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        slices = [dec.slices(n, idx, val, None) for n in range(N)]
+        orders = ([synth.csf_order(idx, n) for n in range(N)] if args.order == "csf"
+                  else [None] * N)
+        slices = [dec.slices(n, idx, val, orders[n]) for n in range(N)]
+        del orders
         torch.cuda.synchronize()
         layout_s = time.perf_counter() - t0
         for sl in slices:
@@ -1021,7 +1039,9 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             for dd, hh in zip(draw, hraw):
                 dd.copy_(hh, non_blocking=True)
             ridx, rval = draw[:N], draw[N]
-            lays = [dec.slices(n, ridx, rval, None) for n in range(N)]
+            lays = [dec.slices(n, ridx, rval,
+                               synth.csf_order(ridx, n) if args.order == "csf" else None)
+                    for n in range(N)]
             for n, sl in enumerate(lays):
                 sl._scratch = None
                 if use_f[n]:
@@ -1059,6 +1079,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 d.set_slice_tiling(args.slice_tile, args.slice_max_direct)
                 if args.long_slices == "subslices":
                     d.set_long_slices(sft.SFT_LONG_SUBSLICES)
+                d.set_blocked_chains(args.blocked_chains == "on")
                 if chain_limits:
                     for sl in slices:
                         d.autotune_slices(sl, lr=lr, lam=0.01)
@@ -1115,7 +1136,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, S = cpu_oracle_epoch_rate(T, args.cpu_sample)
+        rate, dt, S = cpu_oracle_epoch_rate(T, args.cpu_sample, args.order)
         cpu = {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
                "sample": f"first {S} training nonzeros, one epoch ({dt:.1f} s)"}
 
@@ -1131,8 +1152,12 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                 "parallelism": "replicas only" if world > 1 else "single GPU",
                 "path": args.path,
                 "long_slices": args.long_slices if args.path == "slices" else None,
-                "schedule": ("factor: every mode-n slice element by element (Algorithm 4 order, "
-                             "slice layout)" if slices else "factor: Hogwild rows (COO)")
+                "blocked_chains": args.blocked_chains if args.path == "slices" else None,
+                "schedule": (("factor: every mode-n slice element by element (Algorithm 4), "
+                              + ("in the B-CSF traversal order (each slice sorted by the other "
+                                 "modes' coordinates)" if args.order == "csf"
+                                 else "in storage order"))
+                             if slices else "factor: Hogwild rows (COO)")
                             + f"; core: batch {core_batch} (Algorithm 5 when = nnz); refresh "
                               "after every pass; test loss",
                 "layout_build_s": round(layout_s, 3),

@@ -330,6 +330,16 @@ sft_status sft_set_tc_wait_limit(sft_ctx *ctx, int64_t limit_ns);
  *     the row as it stands when the walk starts, and its change is added to
  *     the row with atomic adds.  Pieces of one row overlap in time (Hogwild
  *     within the row), so the result depends on scheduling. */
+/* Blocked chains in the fiber factor pass (sft_update_factors_fibers, J_n in
+ * {8, 16, 32}, lr * lambda < 0.5; on by default): a chain of at least 4096
+ * nonzeros is run by one warp 32 nonzeros at a time -- the block's steps
+ * solved as a triangular system over its Gram matrix V V^T (TF32 tensor-core
+ * MMAs with a high/low split, float32 accumulation), the row moved once per
+ * block.  The same recurrence re-associated: results agree with the
+ * element-by-element form to rounding, not bitwise.  enable = 0 runs every
+ * chain element by element. */
+sft_status sft_set_blocked_chains(sft_ctx *ctx, int32_t enable);
+
 #define SFT_LONG_MAPS 0
 #define SFT_LONG_SUBSLICES 1
 sft_status sft_set_long_slices(sft_ctx *ctx, int32_t how);

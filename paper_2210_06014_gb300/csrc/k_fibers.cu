@@ -340,7 +340,7 @@ static FiberCoords fiber_coords(const PassArgs &a, const int32_t *const *fcoord)
 }
 
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 bool subslices, float *maps, const int32_t *fid,
+                                 bool subslices, bool gram, float *maps, const int32_t *fid,
                                  const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss_in,
                                  int sms, int64_t *launches) {
@@ -382,6 +382,8 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.Lseq = Lseq;
     g.Lhead = subslices ? 0 : Lseq;
     g.subslices = subslices ? 1 : 0;
+    // blocked chains: J_n with an MMA shape, and alpha = 1 - lr lambda well away from 0
+    g.gram = (gram && (J == 8 || J == 16 || J == 32) && a.lr * a.lam < 0.5f) ? 1 : 0;
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     g.fid = fid;
@@ -389,8 +391,11 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.nfibers = nfibers;
     const bool with_maps = maps != nullptr;
     {
-        cudaError_t e = launch_chain_list(g, (char *)maps + slice_maps_bytes(g.ntiles, J), ss.chains,
-                                          sms, launches);
+        cudaError_t e = launch_chain_list(g, (char *)maps + slice_chain_list_offset(g.ntiles, J),
+                                          ss.chains, sms, launches);
+        if (e == cudaSuccess && with_maps && !subslices)
+            e = launch_piece_list(g, (char *)maps + slice_piece_list_offset(g.ntiles, J), ss.maps,
+                                  sms, launches);
         if (e != cudaSuccess) return e;
     }
     factor_slices_fv(g, R, J, with_maps, ss, sms, launches);

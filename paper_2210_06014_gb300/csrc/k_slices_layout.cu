@@ -473,39 +473,94 @@ int slice_core_tile_length(int64_t nnz, int sms) {
 
 // The pass's chain list: every crossing slice (one that spans a tile
 // boundary) of at most Lseq nonzeros, and, when long slices have a head
-// (Lhead > 0), every longer crossing slice too (for its head).
+// (Lhead > 0), every longer crossing slice too (for its head).  A chain of at
+// least gram_min positions (gram_min > 0) is stored from the back of the list
+// (count[1]) for the blocked-chain kernel, shorter ones from the front
+// (count[0]); the list has room for `cap` entries (one per tile boundary).
 __global__ void k_chain_list(const int32_t *__restrict__ row_ptr, int32_t In, int64_t W,
-                             int64_t Lseq, int64_t Lhead, int64_t nnz, int32_t *list,
-                             unsigned int *count) {
+                             int64_t Lseq, int64_t Lhead, int64_t nnz, int64_t gram_min,
+                             int64_t cap, int32_t *list, unsigned int *count) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < In;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = row_ptr[r], e = row_ptr[r + 1];
         if (Lseq <= 0 || s < 0 || s >= e || e > nnz) continue;
         if (e - s > Lseq && Lhead <= 0) continue;
         if (s / W == (e - 1) / W) continue;  // inside one tile: the tile kernel runs it
-        list[atomicAdd(count, 1u)] = (int32_t)r;
+        const int64_t run = e - s <= Lseq ? e - s : Lhead;
+        if (gram_min > 0 && run >= gram_min)
+            list[cap - 1 - atomicAdd(&count[1], 1u)] = (int32_t)r;
+        else
+            list[atomicAdd(&count[0], 1u)] = (int32_t)r;
     }
 }
 
-// list_ws: 16 bytes of count, then room for one row per tile boundary.
+// list_ws: 16 bytes of counts, then room for one row per tile boundary.
 cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
                               int64_t *launches) {
     g.nchains = (unsigned int *)list_ws;
     g.chains = (int32_t *)((char *)list_ws + 16);
-    cudaError_t e = cudaMemsetAsync(g.nchains, 0, sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(g.nchains, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     const int32_t In = g.a.dims[g.a.n];
     int64_t blocks = (In + 255) / 256;
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
     if (blocks < 1) blocks = 1;
-    k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.Lhead, g.a.nnz, g.chains,
-                                               g.nchains);
+    k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.Lhead, g.a.nnz,
+                                               g.gram ? kGramMin : 0,
+                                               g.ntiles < 1 ? 1 : g.ntiles, g.chains, g.nchains);
     *launches += 1;
     return cudaGetLastError();
 }
 
 size_t slice_maps_bytes(int64_t ntiles, int J) {
     return (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * (size_t)(J * J + J) * sizeof(float);
+}
+
+// Workspace of a slice factor pass: the piece maps, the chain list (a count
+// and one row per tile), then the piece list (two counts and two entries per
+// tile), each part starting on a 16-byte boundary.
+size_t slice_chain_list_offset(int64_t ntiles, int J) { return slice_maps_bytes(ntiles, J); }
+
+size_t slice_piece_list_offset(int64_t ntiles, int J) {
+    const size_t o = slice_chain_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 4;
+    return (o + 15) / 16 * 16;
+}
+
+size_t slice_workspace_total(int64_t ntiles, int J) {
+    return slice_piece_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * 4;
+}
+
+// The pass's map pieces into the piece list: full-tile pieces from the front,
+// shorter ones from the back (each piece writes only its own map slot, so the
+// order of the list affects no result).
+__global__ void k_piece_list(SliceArgs g) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        for (int side = 0; side < 2; ++side) {
+            int32_t r;
+            int64_t s, e, hs, q0, q1;
+            if (!map_piece(g, t, side, r, s, e, hs, q0, q1)) continue;
+            const int32_t entry = (int32_t)(t * 2 + side);
+            if (q1 - q0 == g.W) g.pieces[atomicAdd(&g.npieces[0], 1u)] = entry;
+            else g.pieces[2 * g.ntiles - 1 - atomicAdd(&g.npieces[1], 1u)] = entry;
+        }
+    }
+}
+
+// The map pieces of the pass into g.pieces / g.npieces (list_ws: the piece
+// list part of the workspace).
+cudaError_t launch_piece_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                              int64_t *launches) {
+    g.npieces = (unsigned int *)list_ws;
+    g.pieces = (int32_t *)((char *)list_ws + 16);
+    cudaError_t e = cudaMemsetAsync(g.npieces, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (g.ntiles + 255) / 256;
+    if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+    if (blocks < 1) blocks = 1;
+    k_piece_list<<<(int)blocks, 256, 0, st>>>(g);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 template <typename F>
@@ -518,8 +573,9 @@ static void dispatch_nb(int N, F &&f) {
 }
 
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 bool subslices, float *maps, int J, int R,
+                                 bool subslices, bool gram, float *maps, int J, int R,
                                  const SliceStreams &ss_in, int sms, int64_t *launches) {
+    (void)gram;  // the blocked chains read v from the fiber table
     SliceStreams ss = ss_in;
     const cudaStream_t st = ss.tiles;
     const bool fork = ss.fork && ss.chains_done && ss.maps_done && ss.chains && ss.maps &&
@@ -542,8 +598,11 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     g.maps = maps;
     const bool with_maps = maps != nullptr;
     {
-        cudaError_t e = launch_chain_list(g, (char *)maps + slice_maps_bytes(g.ntiles, J), ss.chains,
-                                          sms, launches);
+        cudaError_t e = launch_chain_list(g, (char *)maps + slice_chain_list_offset(g.ntiles, J),
+                                          ss.chains, sms, launches);
+        if (e == cudaSuccess && with_maps && !subslices)
+            e = launch_piece_list(g, (char *)maps + slice_piece_list_offset(g.ntiles, J), ss.maps,
+                                  sms, launches);
         if (e != cudaSuccess) return e;
     }
     if (a.cbf16) {

@@ -45,6 +45,7 @@ struct sft_ctx {
     int tensor_cores = 1;  // tcgen05 refresh / core gradient for bfloat16 cached products
     uint64_t tc_wait_ns = 2000000000ull;  // limit of the tensor-core kernels' waits
     int long_slices = SFT_LONG_MAPS;      // how the slice factor pass runs long slices
+    int blocked_chains = 1;               // long chains of the fiber pass in 32-position blocks
     std::string last_error;
 };
 
@@ -537,8 +538,8 @@ size_t sft_slices_workspace_bytes(const sft_ctx *c, int32_t mode, int64_t nnz) {
     if (!c || mode < 0 || mode >= c->N || nnz < 0) return 0;
     const int64_t W = slice_W(c, nnz);
     const int64_t ntiles = (nnz + W - 1) / W;
-    // the piece maps, then the pass's chain list (a count and one row per tile)
-    return slice_maps_bytes(ntiles, c->J[mode]) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 4;
+    // the piece maps, the pass's chain list and its piece list
+    return slice_workspace_total(ntiles, c->J[mode]);
 }
 
 static sft_status check_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
@@ -566,7 +567,8 @@ sft_status sft_update_factors_slices(sft_ctx *c, int32_t mode, const int32_t *co
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
     cudaError_t e = launch_factor_slices(a, row_ptr, W, slice_Lseq(c, mode, W, nnz),
-                                         c->long_slices == SFT_LONG_SUBSLICES, (float *)workspace,
+                                         c->long_slices == SFT_LONG_SUBSLICES, false,
+                                         (float *)workspace,
                                          c->J[mode], c->R, ss, c->sms, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice factor launch");
     return SFT_OK;
@@ -651,7 +653,8 @@ sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *co
     const int64_t W = slice_W(c, nnz);
     SliceStreams ss{c->stream, c->aux[0], c->aux[1], c->ev[0], c->ev[1], c->ev[2]};
     cudaError_t e = launch_factor_fibers(a, row_ptr, W, slice_Lseq(c, mode, W, nnz),
-                                         c->long_slices == SFT_LONG_SUBSLICES, (float *)workspace,
+                                         c->long_slices == SFT_LONG_SUBSLICES,
+                                         c->blocked_chains != 0, (float *)workspace,
                                          fid, fcoord, nfibers, V, c->J[mode], c->R, ss, c->sms,
                                          &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "fiber factor launch");
@@ -697,6 +700,12 @@ sft_status sft_set_slice_tiling(sft_ctx *c, int64_t tile, int64_t max_direct) {
 sft_status sft_set_tensor_cores(sft_ctx *c, int32_t enable) {
     if (!c) return SFT_EINVAL;
     c->tensor_cores = enable ? 1 : 0;
+    return SFT_OK;
+}
+
+sft_status sft_set_blocked_chains(sft_ctx *c, int32_t enable) {
+    if (!c) return SFT_EINVAL;
+    c->blocked_chains = enable ? 1 : 0;
     return SFT_OK;
 }
 

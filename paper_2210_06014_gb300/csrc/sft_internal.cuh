@@ -83,13 +83,16 @@ struct SliceStreams {
 // slice (CSF) layout and the passes over it
 int64_t slice_sort_length(int64_t nnz);
 size_t slice_maps_bytes(int64_t ntiles, int J);
+size_t slice_chain_list_offset(int64_t ntiles, int J);
+size_t slice_piece_list_offset(int64_t ntiles, int J);
+size_t slice_workspace_total(int64_t ntiles, int J);
 int slice_tile_length(int64_t nnz, int sms);
 int slice_core_tile_length(int64_t nnz, int sms);
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches);
 cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 bool subslices, float *maps, int J, int R, const SliceStreams &ss, int sms,
+                                 bool subslices, bool gram, float *maps, int J, int R, const SliceStreams &ss, int sms,
                                  int64_t *launches);
 cudaError_t launch_core_slices(const PassArgs &a, const int32_t *row_ptr, int64_t W, int J, int R,
                                float *partials, int max_blocks, cudaStream_t st, int sms,
@@ -104,7 +107,7 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
                                 void *scratch, int64_t *nfibers, cudaStream_t st, int sms,
                                 int64_t *launches);
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
-                                 bool subslices, float *maps, const int32_t *fid, const int32_t *const *fcoord,
+                                 bool subslices, bool gram, float *maps, const int32_t *fid, const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss,
                                  int sms, int64_t *launches);
 cudaError_t launch_core_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W,

@@ -16,6 +16,13 @@
 #ifndef SFT_MAP_RING_D
 #define SFT_MAP_RING_D 4
 #endif
+// one-lane chains: prefetch distance and packed partial sums of a . v
+#ifndef SFT_LANE_CHAIN_P
+#define SFT_LANE_CHAIN_P 16
+#endif
+#ifndef SFT_LANE_DOT_PACKED
+#define SFT_LANE_DOT_PACKED 1
+#endif
 
 namespace sft {
 
@@ -168,11 +175,17 @@ struct SliceArgs {
     int64_t Lhead;           // head of a long slice run as a chain before its map region
                              // (= Lseq for the exact maps; 0 for sub-slices)
     int subslices;           // long slices as concurrent sub-slices (no maps)
+    // the pass's map pieces, as t * 2 + slot: full-tile pieces, then shorter
+    // ones (built by k_piece_list, so that the groups of a warp run pieces of
+    // the same length side by side)
+    int32_t *pieces;         // [2 * ntiles] full pieces from the front, short from the back
+    unsigned int *npieces;   // [0]: full pieces, [1]: short pieces
     int64_t ntiles;
     float *maps;             // [ntiles][2][J*J + J]
     // crossing slices of at most Lseq nonzeros (built per pass by k_chain_list)
-    int32_t *chains;         // their rows, in no particular order
-    unsigned int *nchains;   // how many
+    int32_t *chains;         // their rows, in no particular order (blocked chains from the back)
+    unsigned int *nchains;   // [0]: chains for the lane kernels, [1]: for the blocked kernel
+    int gram;                // long chains run by the blocked (Gram) kernel
     // fiber-shared v (set for the fiber variant of the factor pass)
     const int32_t *fid;      // fiber of every slice position (-1: bad data)
     const float *V;          // [nfibers][J]: v = B^(n) p of every fiber
@@ -581,12 +594,27 @@ template <int T, int J>
 __device__ __forceinline__ float group_order_dot(const float (&a)[J], const float (&v)[J]) {
     constexpr int JL = J / T;
     float p[T];
+    if constexpr (T % 2 == 0 && SFT_LANE_DOT_PACKED) {
+        // two group lanes' partial sums at a time with packed FMAs (each half
+        // an ordinary fused multiply-add, in the same order as a lane's sum)
 #pragma unroll
-    for (int l = 0; l < T; ++l) {
-        float d = 0.f;
+        for (int l = 0; l < T; l += 2) {
+            float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < JL; ++q) d = fmaf(a[l * JL + q], v[l * JL + q], d);
-        p[l] = d;
+            for (int q = 0; q < JL; ++q)
+                d = __ffma2_rn(make_float2(a[l * JL + q], a[(l + 1) * JL + q]),
+                               make_float2(v[l * JL + q], v[(l + 1) * JL + q]), d);
+            p[l] = d.x;
+            p[l + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < T; ++l) {
+            float d = 0.f;
+#pragma unroll
+            for (int q = 0; q < JL; ++q) d = fmaf(a[l * JL + q], v[l * JL + q], d);
+            p[l] = d;
+        }
     }
     // butterfly: at distance w every member adds its partner's value
 #pragma unroll
@@ -605,14 +633,15 @@ __device__ __forceinline__ float group_order_dot(const float (&a)[J], const floa
 // walk) and 2P positions of the scalars (fiber id, value, mode-n coordinate).
 template <int J, int P, bool ROWS>
 struct LaneRing {
-    static constexpr int DV = P + 1;
-    static constexpr int DS = 2 * P + 1;
+    // a slot is refilled two positions after it was read
+    static constexpr int DV = P + 2;
+    static constexpr int DS = 2 * P + 2;
     static constexpr int VW = ROWS ? 2 * J : J;  // floats per v slot
     static constexpr int words = (DV * VW + 3 * DS + 3) / 4 * 4;  // 16-byte multiple
 };
 
 constexpr int kLaneThreads = 64;  // block size of the one-lane kernels
-constexpr int kLaneChainP = 16;   // prefetch distance of a chain
+constexpr int kLaneChainP = SFT_LANE_CHAIN_P;  // prefetch distance of a chain
 constexpr int kLaneTileP = 8;     // ... of a tile walk (its slots also hold rows)
 
 // Calls body(row, x, ok, v, newrow) for positions [s0, s1) in order: v = the
@@ -624,26 +653,30 @@ __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64
                                           Body &&body) {
     using LR = LaneRing<J, P, ROWS>;
     constexpr int DV = LR::DV, DS = LR::DS, VW = LR::VW;
+    static_assert(P % 2 == 0, "two positions per wait");
     const PassArgs &a = g.a;
     float *vr = ring;
     int32_t *fr = reinterpret_cast<int32_t *>(ring + DV * VW);
     float *xr = ring + DV * VW + DS;
     int32_t *rr = reinterpret_cast<int32_t *>(ring + DV * VW + 2 * DS);
-    const int64_t n = s1 - s0;
+    const int n = (int)(s1 - s0);  // a walk stays inside one pass (< 2^31 positions)
+    const int32_t *fid = g.fid + s0;
+    const float *val = a.val + s0;
+    const int32_t *rowi = a.idx[a.n] + s0;
     const uint32_t In = (uint32_t)a.dims[a.n];
+    const uint32_t nf = (uint32_t)g.nfibers;  // < 2^31 (one fiber per position at most)
     int32_t last_row = -1;  // coordinate of the last position whose v copy was issued
-    auto scalars = [&](int64_t q, int slot) {
+    auto scalars = [&](int q, int slot) {
         if (q < n) {
-            cp_async<4>(fr + slot, g.fid + s0 + q);
-            cp_async<4>(xr + slot, a.val + s0 + q);
-            if constexpr (ROWS) cp_async<4>(rr + slot, a.idx[a.n] + s0 + q);
+            cp_async<4>(fr + slot, fid + q);
+            cp_async<4>(xr + slot, val + q);
+            if constexpr (ROWS) cp_async<4>(rr + slot, rowi + q);
         }
     };
-    auto vcopy = [&](int64_t q, int fslot, int vslot) {
+    auto vcopy = [&](int q, int fslot, int vslot) {
         if (q < n) {
             const int32_t f = fr[fslot];
-            if ((uint64_t)(int64_t)f < (uint64_t)g.nfibers)
-                cp_async<J * 4>(vr + vslot * VW, g.V + (int64_t)f * J);
+            if ((uint32_t)f < nf) cp_async<J * 4>(vr + vslot * VW, g.V + (int64_t)f * J);
             if constexpr (ROWS) {
                 const int32_t r = rr[fslot];
                 if (r != last_row && (uint32_t)r < In)
@@ -652,17 +685,7 @@ __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64
             }
         }
     };
-    for (int q = 0; q < P; ++q) scalars(q, q);
-    cp_async_commit();
-    cp_async_wait<0>();
-    for (int q = 0; q < P; ++q) {
-        vcopy(q, q, q);
-        scalars(q + P, q + P);
-        cp_async_commit();
-    }
-    int vs = 0, ss = 0, fs = P;
-    for (int64_t i = 0; i < n; ++i) {
-        cp_async_wait<P - 1>();  // this lane's copies of step i - P have landed
+    auto use = [&](int ss, int vs) {
         const int32_t f = fr[ss];
         const float x = xr[ss];
         int32_t row = ROWS ? rr[ss] : -1;
@@ -673,21 +696,42 @@ __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64
             const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
             v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
         }
-        bool ok = (uint64_t)(int64_t)f < (uint64_t)g.nfibers;
+        bool ok = (uint32_t)f < nf;
         if (ROWS && (uint32_t)row >= In) {
             ok = false;
             row = -1;
         }
         if (!ok) atomicOr(a.err, kErrIndex);
-        body(row, x, ok, v, src + J);  // reads the slot before it is refilled below
-        const int prev_vs = vs == 0 ? DV - 1 : vs - 1;
-        const int prev_ss = ss == 0 ? DS - 1 : ss - 1;
-        vcopy(i + P, fs, prev_vs);
-        scalars(i + 2 * P, prev_ss);
+        body(row, x, ok, v, src + J);  // reads the slot before it is refilled
+    };
+    auto next = [](int x, int D) { return x + 1 == D ? 0 : x + 1; };
+    for (int q = 0; q < P; ++q) scalars(q, q);
+    cp_async_commit();
+    cp_async_wait<0>();
+    for (int q = 0; q < P; ++q) {
+        vcopy(q, q, q);
+        scalars(q + P, q + P);
         cp_async_commit();
-        vs = vs + 1 == DV ? 0 : vs + 1;
-        ss = ss + 1 == DS ? 0 : ss + 1;
-        fs = fs + 1 == DS ? 0 : fs + 1;
+    }
+    int vs = 0, ss = 0;             // slots of position i
+    int fs = P;                     // scalar slot of position i + P
+    int rv = DV - 2, rs = DS - 2;   // slots of position i - 2, refilled at step i
+    auto advance = [&]() {
+        vs = next(vs, DV); ss = next(ss, DS); fs = next(fs, DS);
+        rv = next(rv, DV); rs = next(rs, DS);
+    };
+    for (int i = 0; i < n; i += 2) {
+        cp_async_wait<P - 2>();  // this lane's copies of steps i - P and i + 1 - P have landed
+        use(ss, vs);             // position i
+        vcopy(i + P, fs, rv);
+        scalars(i + 2 * P, rs);
+        cp_async_commit();
+        advance();
+        if (i + 1 < n) use(ss, vs);  // position i + 1
+        vcopy(i + 1 + P, fs, rv);
+        scalars(i + 1 + 2 * P, rs);
+        cp_async_commit();
+        advance();
     }
     cp_async_wait<0>();
 }
@@ -700,8 +744,18 @@ __device__ __forceinline__ void lane_step(const PassArgs &a, float (&av)[J], con
                                           float x, bool ok) {
     const float e = x - group_order_dot<T, J>(av, v);
     if (ok) {
+        // row_step on pairs of entries with packed float32 operations (the
+        // same roundings as row_step entry by entry)
+        const float2 e2 = make_float2(e, e), nl = make_float2(-a.lam, -a.lam),
+                     lr = make_float2(a.lr, a.lr);
 #pragma unroll
-        for (int q = 0; q < J; ++q) av[q] = row_step(av[q], e, v[q], a.lr, a.lam);
+        for (int q = 0; q < J; q += 2) {
+            const float2 aq = make_float2(av[q], av[q + 1]);
+            const float2 d = __ffma2_rn(nl, aq, __fmul2_rn(e2, make_float2(v[q], v[q + 1])));
+            const float2 r = __ffma2_rn(lr, d, aq);
+            av[q] = r.x;
+            av[q + 1] = r.y;
+        }
     }
 }
 
@@ -782,6 +836,278 @@ __global__ void __launch_bounds__(kLaneThreads) k_slices_tiles1(SliceArgs g) {
             lane_step<T, J>(a, av, v, x, ok);
         });
         if (cur >= 0) store_run<J>(a.A + (int64_t)cur * J, av);
+    }
+}
+
+// ============================================================================ factor: blocked chains
+// A long element-by-element chain (a crossing slice run whole, or the head of
+// a long slice) is run by one warp, 32 positions at a time.  With every v of a
+// block known in advance, the block's steps collapse to a triangular solve:
+// writing a_t for the row before the t-th position of the block, c_t for the
+// number of valid positions before it, alpha = 1 - lr lambda, beta = lr/alpha,
+// u_t = a_0 . v_t and G_tk = v_t . v_k, the scaled residuals
+// g_t = e_t / alpha^c_t satisfy
+//   g_t = x_t alpha^-c_t - u_t - beta sum_{k < t} G_tk g_k
+// (Eq. (10) applied position after position, Algorithm 4's order), and the row
+// after the block is a_B = alpha^c_B (a_0 + beta sum_t g_t v_t).  The Gram
+// block G = V V^T (32 x 32, K = J_n) is a real contraction: it runs on the
+// tensor cores (mma.sync m16n8k8, TF32 operands split into high and low
+// parts, three products, float32 accumulation: about float32 accuracy); the
+// solve is 32 broadcast-and-FMA steps across the warp, the sums over the block
+// are float32.  The inputs are staged PB blocks ahead with cp.async (fiber
+// ids 2 PB blocks ahead).  Invalid positions (bad fiber id, or past the end of
+// the chain) have v = 0 and are not counted in c_t.
+constexpr int kGramWarps = 4;      // chains (warps) per block
+constexpr int kGramPB = 3;         // prefetch distance in 32-position blocks
+constexpr int64_t kGramMin = 4096;  // shortest chain given to the blocked kernel
+
+template <int J>
+struct GramSmem {
+    static constexpr int SV = J + 4;           // v row stride (conflict-free fragment loads)
+    static constexpr int SG = 36;              // Gram row stride
+    static constexpr int NVB = kGramPB + 1;    // v / x block slots
+    static constexpr int NFB = 2 * kGramPB + 1;  // fiber-id block slots
+    static constexpr int v_words = NVB * 32 * SV;
+    static constexpr int x_words = NVB * 32;
+    static constexpr int f_words = NFB * 32;
+    static constexpr int g_words = 32 * SG;
+    static constexpr int w_words = 32;
+    static constexpr int words = v_words + x_words + f_words + g_words + w_words;  // per warp
+    static constexpr size_t bytes = (size_t)kGramWarps * words * 4 + 2 * 33 * 4;    // + alpha tables
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// G' = V (beta V)^T for the 32 x J block V (rows = positions, stride SV), into
+// sg (row-major, stride SG).  Fragments of m16n8k8 (TF32): A rows gid, gid + 8
+// and columns tig, tig + 4 of a 16 x 8 tile; B rows (k) tig, tig + 4 and
+// column gid; D rows gid, gid + 8 and columns 2 tig, 2 tig + 1
+// (gid = lane / 4, tig = lane % 4).
+template <int J>
+__device__ __forceinline__ void gram_block(const float *vb, float beta, float *sg, int lane) {
+    constexpr int SV = GramSmem<J>::SV, SG = GramSmem<J>::SG;
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[mi][ni][q] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < J / 8; ++kk) {
+        uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const float x[4] = {vb[(16 * mi + gid) * SV + 8 * kk + tig],
+                                vb[(16 * mi + gid + 8) * SV + 8 * kk + tig],
+                                vb[(16 * mi + gid) * SV + 8 * kk + tig + 4],
+                                vb[(16 * mi + gid + 8) * SV + 8 * kk + tig + 4]};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ah[mi][q] = to_tf32(x[q]);
+                al[mi][q] = to_tf32(x[q] - __uint_as_float(ah[mi][q]));
+            }
+        }
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const float y[2] = {beta * vb[(8 * ni + gid) * SV + 8 * kk + tig],
+                                beta * vb[(8 * ni + gid) * SV + 8 * kk + tig + 4]};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                bh[ni][q] = to_tf32(y[q]);
+                bl[ni][q] = to_tf32(y[q] - __uint_as_float(bh[ni][q]));
+            }
+        }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                mma_tf32(acc[mi][ni], al[mi], bh[ni]);
+                mma_tf32(acc[mi][ni], ah[mi], bl[ni]);
+                mma_tf32(acc[mi][ni], ah[mi], bh[ni]);
+            }
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const int r0 = 16 * mi + gid, c0 = 8 * ni + 2 * tig;
+            *reinterpret_cast<float2 *>(sg + r0 * SG + c0) = make_float2(acc[mi][ni][0], acc[mi][ni][1]);
+            *reinterpret_cast<float2 *>(sg + (r0 + 8) * SG + c0) =
+                make_float2(acc[mi][ni][2], acc[mi][ni][3]);
+        }
+}
+
+// The chains of at least kGramMin positions from the back of the chain list,
+// one per warp.
+template <int J>
+__global__ void __launch_bounds__(kGramWarps * 32) k_slices_gram(SliceArgs g) {
+    using GS = GramSmem<J>;
+    constexpr int SV = GS::SV, SG = GS::SG, NVB = GS::NVB, NFB = GS::NFB, PB = kGramPB;
+    extern __shared__ __align__(16) float gram_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *apow = gram_smem + kGramWarps * GS::words;  // alpha^k, k = 0..32
+    float *ainv = apow + 33;                            // alpha^-k
+    const PassArgs &a = g.a;
+    const float alpha = 1.f - a.lr * a.lam;
+    const float beta = a.lr / alpha;
+    if (threadIdx.x == 0) {
+        float p = 1.f, q = 1.f;
+        const float ai = 1.f / alpha;
+        for (int k = 0; k <= 32; ++k) {
+            apow[k] = p;
+            ainv[k] = q;
+            p *= alpha;
+            q *= ai;
+        }
+    }
+    __syncthreads();
+    float *base = gram_smem + warp * GS::words;
+    float *vbuf = base;                                        // [NVB][32][SV]
+    float *xbuf = vbuf + GS::v_words;                          // [NVB][32]
+    int32_t *fbuf = reinterpret_cast<int32_t *>(xbuf + GS::x_words);  // [NFB][32]
+    float *sg = reinterpret_cast<float *>(fbuf + GS::f_words);  // [32][SG]
+    float *wv = sg + GS::g_words;                               // [32]
+    const uint32_t nf = (uint32_t)g.nfibers;
+    const int64_t nlong = (int64_t)g.nchains[1];
+    const int64_t cap = g.ntiles;  // list capacity: long chains are stored from the back
+    const int64_t warps = (int64_t)gridDim.x * kGramWarps;
+    // chains fill the blocks in order (four per block), so that blocks past the
+    // list exit at once and give their shared memory back to the other kernels
+    for (int64_t c = (int64_t)blockIdx.x * kGramWarps + warp; c < nlong; c += warps) {
+        const int32_t r = __ldg(g.chains + cap - 1 - c);
+        if ((uint32_t)r >= (uint32_t)a.dims[a.n]) continue;
+        const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+        if (!slice_ok(g, s, e)) continue;
+        const int64_t e1 = e - s <= g.Lseq ? e : min(e, s + g.Lhead);
+        const int n = (int)(e1 - s);
+        const int nb = (n + 31) >> 5;
+        const int32_t *fid = g.fid + s;
+        const float *val = a.val + s;
+        // staging of block b: fiber ids (2 PB blocks ahead), then v and x (PB ahead)
+        auto fids = [&](int b) {
+            const int p = 32 * b + lane;
+            if (b < nb && p < n) cp_async<4>(fbuf + (b % NFB) * 32 + lane, fid + p);
+        };
+        auto vx = [&](int b) {
+            if (b >= nb) return;
+            const int p = 32 * b + lane;
+            float *dst = vbuf + (b % NVB) * 32 * SV + lane * SV;
+            const int32_t f = p < n ? fbuf[(b % NFB) * 32 + lane] : -1;
+            if (p < n && (uint32_t)f < nf) {
+                cp_async<J * 4>(dst, g.V + (int64_t)f * J);
+                cp_async<4>(xbuf + (b % NVB) * 32 + lane, val + p);
+            } else {
+#pragma unroll
+                for (int q = 0; q < J; q += 4)
+                    *reinterpret_cast<float4 *>(dst + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+                xbuf[(b % NVB) * 32 + lane] = 0.f;
+            }
+        };
+        for (int b = 0; b < PB; ++b) fids(b);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        for (int b = 0; b < PB; ++b) {
+            vx(b);
+            fids(b + PB);
+            cp_async_commit();
+        }
+        // the row, in every lane
+        float av[J];
+        {
+            const float *arow = a.A + (int64_t)r * J;
+#pragma unroll
+            for (int q = 0; q < J; q += 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(arow + q);
+                av[q] = t4.x; av[q + 1] = t4.y; av[q + 2] = t4.z; av[q + 3] = t4.w;
+            }
+        }
+        float a_own = 0.f;  // av[lane % J] after the last block
+        for (int b = 0; b < nb; ++b) {
+            cp_async_wait<PB - 1>();  // this lane's copies of block b have landed
+            __syncwarp();             // ... and every lane's; slots of block b - 1 are free
+            vx(b + PB);
+            fids(b + 2 * PB);
+            cp_async_commit();
+            const float *vb = vbuf + (b % NVB) * 32 * SV;
+            const int p = 32 * b + lane;
+            const int32_t f = p < n ? fbuf[(b % NFB) * 32 + lane] : -1;
+            const bool valid = p < n && (uint32_t)f < nf;
+            if (p < n && !valid) atomicOr(a.err, kErrIndex);
+            const unsigned mask = __ballot_sync(kFull, valid);
+            // u = a . v of the lane's position (the solve's right-hand side)
+            float vl[J];
+#pragma unroll
+            for (int q = 0; q < J; q += 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(vb + lane * SV + q);
+                vl[q] = t4.x; vl[q + 1] = t4.y; vl[q + 2] = t4.z; vl[q + 3] = t4.w;
+            }
+            float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < J; q += 2) {
+                u0 = fmaf(av[q], vl[q], u0);
+                u1 = fmaf(av[q + 1], vl[q + 1], u1);
+            }
+            const int ct = __popc(mask & ((1u << lane) - 1u));
+            float rr = valid ? fmaf(xbuf[(b % NVB) * 32 + lane], ainv[ct], -(u0 + u1)) : 0.f;
+            // G' = beta V V^T on the tensor cores, then the lane's row of it
+            gram_block<J>(vb, beta, sg, lane);
+            __syncwarp();
+            float h[32];
+#pragma unroll
+            for (int k = 0; k < 32; k += 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(sg + lane * SG + k);
+                h[k] = t4.x; h[k + 1] = t4.y; h[k + 2] = t4.z; h[k + 3] = t4.w;
+            }
+            // forward substitution: g_k is final in lane k when step k is reached
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float gk = __shfl_sync(kFull, rr, k);
+                if (lane > k) rr = fmaf(-h[k], gk, rr);
+            }
+            // the row after the block: alpha^c_B (a + beta sum_t g_t v_t)
+            wv[lane] = valid ? rr : 0.f;
+            __syncwarp();
+            float sj;
+            {
+                constexpr int SPL = 32 / J;  // lanes per entry j, each summing 32/SPL positions
+                const int j = lane % J, part = lane / J;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = part * (32 / SPL); t < (part + 1) * (32 / SPL); ++t)
+                    acc = fmaf(wv[t], vb[t * SV + j], acc);
+#pragma unroll
+                for (int w = J; w < 32; w <<= 1) acc += __shfl_xor_sync(kFull, acc, w);
+                sj = acc;
+            }
+            const float ab = apow[__popc(mask)];
+            float aj = av[0];  // av[lane % J], selected without a dynamic register index
+#pragma unroll
+            for (int q = 1; q < J; ++q)
+                if ((lane % J) == q) aj = av[q];
+            const float anew = ab * fmaf(beta, sj, aj);
+            a_own = anew;
+#pragma unroll
+            for (int q = 0; q < J; ++q) av[q] = __shfl_sync(kFull, anew, q);
+            __syncwarp();  // sg / wv are rewritten by the next block
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+        if (lane < J && nb > 0) a.A[(int64_t)r * J + lane] = a_own;
     }
 }
 
@@ -1091,7 +1417,7 @@ __device__ __forceinline__ bool map_piece(const SliceArgs &g, int64_t t, int sid
     return true;
 }
 
-// One group per tile: the tile's map pieces (at most one per slot).
+// One group per map piece of the piece list (full pieces first).
 template <bool FV, int NB, int R, int J, typename CT>
 __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(SliceArgs g) {
     constexpr int T = R / 4;
@@ -1107,15 +1433,18 @@ __global__ void __launch_bounds__(kSliceThreads, SFT_MAPS_MINB) k_slices_maps(Sl
     const unsigned m = group_mask<T>(lane);
     float *ring = RINGED ? sring + (threadIdx.x / T) * (MapRing<R, J>::D * J) : nullptr;
     const int64_t groups = (int64_t)gridDim.x * GPB;
-    for (int64_t t = (int64_t)blockIdx.x * GPB + threadIdx.x / T; t < g.ntiles;
-         t += groups) {
-        for (int side = 0; side < 2; ++side) {
-            int32_t r;
-            int64_t s, e, hs, q0, q1;
-            if (!map_piece(g, t, side, r, s, e, hs, q0, q1)) continue;
-            compose_map<FV, NB, R, J, CT>(g, sB, ring, q0, q1, sub, m,
-                                          g.maps + (t * 2 + side) * (int64_t)(J * J + J));
-        }
+    const int64_t nfull = (int64_t)g.npieces[0], nshort = (int64_t)g.npieces[1];
+    for (int64_t k = (int64_t)blockIdx.x * GPB + threadIdx.x / T; k < nfull + nshort;
+         k += groups) {
+        const int32_t entry = k < nfull ? __ldg(g.pieces + k)
+                                        : __ldg(g.pieces + 2 * g.ntiles - 1 - (k - nfull));
+        const int64_t t = entry >> 1;
+        const int side = entry & 1;
+        int32_t r;
+        int64_t s, e, hs, q0, q1;
+        if (t >= g.ntiles || !map_piece(g, t, side, r, s, e, hs, q0, q1)) continue;
+        compose_map<FV, NB, R, J, CT>(g, sB, ring, q0, q1, sub, m,
+                                      g.maps + (t * 2 + side) * (int64_t)(J * J + J));
     }
 }
 
@@ -1313,9 +1642,22 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
         cudaFuncSetAttribute(k_slices_tiles1<R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tsm);
         if (g.ntiles > 1) {
+            if constexpr (J == 8 || J == 16 || J == 32) {
+                if (g.gram) {
+                    // the blocked chains first, on their own stream: they are the
+                    // longest dependent sequences of the pass
+                    cudaFuncSetAttribute(k_slices_gram<J>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GramSmem<J>::bytes);
+                    const int gg = grid_for(k_slices_gram<J>, kGramWarps * 32, GramSmem<J>::bytes,
+                                            kGramWarps, g.ntiles - 1, sms);
+                    k_slices_gram<J><<<gg, kGramWarps * 32, GramSmem<J>::bytes, ss.chains>>>(g);
+                    *launches += 1;
+                }
+            }
             const int gch = grid_for(k_slices_chains1<R, J>, kLaneThreads, csm, kLaneThreads,
                                      g.ntiles - 1, sms);
-            k_slices_chains1<R, J><<<gch, kLaneThreads, csm, ss.chains>>>(g);
+            k_slices_chains1<R, J><<<gch, kLaneThreads, csm, g.gram ? ss.tiles : ss.chains>>>(g);
             *launches += 1;
         }
         const int gd = grid_for(k_slices_tiles1<R, J>, kLaneThreads, tsm, kLaneThreads, g.ntiles,
@@ -1377,6 +1719,8 @@ SFT_SLICE_WRAPPERS(15, bf16)
 #undef SFT_SLICE_WRAPPERS
 cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms);
 cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                              int64_t *launches);
+cudaError_t launch_piece_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
                               int64_t *launches);
 // fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
 void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,

@@ -38,7 +38,7 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_batch_set_wait_limit", "sft_batch_hold_pass", "sft_fibers_scratch_bytes",
             "sft_group_fibers", "sft_update_factors_fibers", "sft_update_core_fibers",
             "sft_autotune_slices", "sft_set_tensor_cores", "sft_set_tc_wait_limit",
-            "sft_set_long_slices"]
+            "sft_set_long_slices", "sft_set_blocked_chains"]
 
 
 class SftError(RuntimeError):
@@ -135,6 +135,8 @@ def load(build_if_missing: bool = True):
     lib.sft_set_tc_wait_limit.restype = ctypes.c_int
     lib.sft_set_long_slices.argtypes = [ctx, i32]
     lib.sft_set_long_slices.restype = ctypes.c_int
+    lib.sft_set_blocked_chains.argtypes = [ctx, i32]
+    lib.sft_set_blocked_chains.restype = ctypes.c_int
     lib.sft_update_factors_noalloc.argtypes = [
         i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), i32, i32, vp, vp,
         ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, i64, f32, f32, vp]
@@ -371,6 +373,11 @@ def sft_set_long_slices(ctx, how: int) -> None:
     _check(lib, ctx, lib.sft_set_long_slices(ctx, int(how)), "sft_set_long_slices")
 
 
+def sft_set_blocked_chains(ctx, enable: bool = True) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sft_set_blocked_chains(ctx, 1 if enable else 0), "sft_set_blocked_chains")
+
+
 def sft_set_tc_wait_limit(ctx, limit_ns: int) -> None:
     lib = load()
     _check(lib, ctx, lib.sft_set_tc_wait_limit(ctx, int(limit_ns)), "sft_set_tc_wait_limit")
@@ -570,6 +577,10 @@ class Decomposition:
 
     def set_slice_tiling(self, tile: int = 0, max_direct: int = 0):
         sft_set_slice_tiling(self.ctx, tile, max_direct)
+
+    def set_blocked_chains(self, enable: bool = True):
+        """Long chains of the fiber pass in 32-position blocks (default) or not."""
+        sft_set_blocked_chains(self.ctx, enable)
 
     def set_long_slices(self, how: int):
         """SFT_LONG_MAPS (exact, default) or SFT_LONG_SUBSLICES (B-CSF style)."""

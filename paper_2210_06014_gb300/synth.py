@@ -344,3 +344,20 @@ def pass_permutation(seed: int, epoch: int, phase: int, mode: int, n: int, devic
     (epoch, phase, mode); phase 0 = factor module, 1 = core module.  uint32
     values are returned in an int32 tensor (n < 2^31)."""
     return permutation(stream_key(seed, 100, epoch, phase, mode), n, device).to(torch.int32)
+
+
+def csf_order(idx, n: int) -> torch.Tensor:
+    """Visit order of the paper's B-CSF traversal for mode n (Section "Tensor
+    Storage Format"): the nonzeros sorted by i_n, then by the other modes'
+    coordinates in ascending mode order (lexicographically), as a CSF tree
+    rooted at mode n is walked.  Returned like pass_permutation (int32
+    tensor holding the uint32 permutation, on the device of idx).  Only an
+    ordering of the input: it carries none of the method's arithmetic."""
+    N = len(idx)
+    keys = [n] + [k for k in range(N) if k != n]
+    order = torch.arange(idx[0].numel(), device=idx[0].device, dtype=torch.int64)
+    # successive stable sorts from the least significant key to the most
+    for k in reversed(keys):
+        _, o = torch.sort(idx[k][order], stable=True)
+        order = order[o]
+    return order.to(torch.int32)

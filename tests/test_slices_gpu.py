@@ -451,6 +451,7 @@ def test_fiber_pass_equals_row_pass(sft, case):
     for use_fibers in (False, True):
         dec = sft.Decomposition(T.A0, T.B0, prec=prec)
         dec.set_slice_tiling(*tiling)
+        dec.set_blocked_chains(False)  # element by element on both sides
         for n in range(N):
             sl = dec.slices(n, idx, val, None)
             if use_fibers:
@@ -570,3 +571,58 @@ def test_subslice_mode_epochs_rmse(sft, oracle_mod):
         want.append(ref.rmse(ix, xv))
     print("sub-slice epochs rmse gpu", got, "oracle", want)
     np.testing.assert_allclose(got, want, rtol=0.01)
+
+
+@pytest.mark.parametrize("tiling", [(64, 1 << 30), (0, 8192), (32, 4100)])
+def test_blocked_chains_match_oracle(sft, oracle_mod, skewed, tiling):
+    """Chains of 4096 or more nonzeros run 32 at a time (Gram block on the tensor
+    cores + triangular solve): every row within the per-row rounding bound of
+    the oracle's sequential pass.  (64, 1 << 30): every crossing slice whole
+    (the Zipf heads of the user and item modes hold 10k+ nonzeros); (0, 8192):
+    heads of 8192 before the maps; (32, 4100): heads of 4100 (not a multiple
+    of 32) before the maps."""
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    dec.set_slice_tiling(*tiling)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        sl = dec.slices(n, idx, val, None)
+        sl.build_fibers(dec)
+        dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+        dec.refresh(n)
+        dec.sync(60_000)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), perm=None, batch=1, lr=0.01,
+                                        lam=0.01)
+        ref.refresh(n)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got))
+        worst = assert_rows_within(got, ref.A[n], S1, S2, what=f"blocked {tiling} A^({n})")
+        print(f"blocked chains {tiling} mode {n}: worst err/bound {worst:.3g}")
+
+
+def test_csf_order_pass_matches_oracle(sft, oracle_mod, skewed):
+    """Slices laid out in the B-CSF traversal order (each slice sorted by the
+    other modes' coordinates, synth.csf_order) with fibers, blocked chains and
+    maps: every row within the per-row bound of the oracle's sequential pass
+    over the same order."""
+    from paper_2210_06014_gb300 import synth
+    T = skewed
+    idx, val = to_dev(T)
+    ix = np_idx(T.idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
+    for n in range(3):
+        order = synth.csf_order(idx, n)
+        sl = dec.slices(n, idx, val, order)
+        sl.build_fibers(dec)
+        dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+        dec.refresh(n)
+        dec.sync(60_000)
+        S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(),
+                                        perm=order.cpu().numpy().astype(np.uint32), batch=1,
+                                        lr=0.01, lam=0.01)
+        ref.refresh(n)
+        got = dec.A[n].cpu().numpy().astype(np.float64)
+        assert_rows_within(got, ref.A[n], S1, S2, what=f"csf order A^({n})")
