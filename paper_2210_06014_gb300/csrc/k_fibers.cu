@@ -9,9 +9,12 @@
 //
 // Fiber ids (layout time): the exact 64-bit linear key of the tuple is
 // inserted into an open-addressing table (atomicCAS, linear probing, bounded
-// by the table size, which is at least twice the number of nonzeros); the
-// occupied slots are then numbered by an atomic counter.  Ids therefore depend
-// on scheduling, but each fiber's v does not, so results are reproducible.
+// by the table size, which is at least twice the number of nonzeros), which
+// also keeps the first layout position of each fiber (atomicMin); fibers are
+// then numbered in the order of their first positions (a scan over the
+// positions), so that a walk over the layout meets fibers it has not seen
+// before in increasing order and reads their v rows as a stream.  Ids do not
+// depend on scheduling, and each fiber's v does not depend on its id.
 //
 // Per pass: k_fiber_v forms every fiber's v with the same arithmetic, in the
 // same order, as the per-nonzero path (product of the other modes' rows in
@@ -50,14 +53,16 @@ struct FiberCoordsOut {
     int32_t *c[kMaxOrder];
 };
 
-__global__ void k_fiber_clear(unsigned long long *table, int64_t cap) {
+__global__ void k_fiber_clear(unsigned long long *table, int32_t *slot_pos, int64_t cap) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-         i += (int64_t)gridDim.x * blockDim.x)
+         i += (int64_t)gridDim.x * blockDim.x) {
         table[i] = kEmpty;
+        slot_pos[i] = 0x7fffffff;
+    }
 }
 
 // slot_of[t] = table slot of position t's fiber (-1 for bad coordinates);
-// the first position to claim a slot is recorded as the fiber's representative.
+// slot_pos[slot] = the fiber's first layout position (its representative).
 __global__ void k_fiber_insert(FiberKeyArgs f, int64_t nnz, unsigned long long *table,
                                int32_t *slot_pos, int64_t cap, int32_t *slot_of, int *err) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz;
@@ -78,12 +83,8 @@ __global__ void k_fiber_insert(FiberKeyArgs f, int64_t nnz, unsigned long long *
         int32_t slot = -1;
         for (int64_t probe = 0; probe < cap; ++probe) {
             const unsigned long long prev = atomicCAS(table + h, kEmpty, key);
-            if (prev == kEmpty) {
-                slot_pos[h] = (int32_t)t;
-                slot = (int32_t)h;
-                break;
-            }
-            if (prev == key) {
+            if (prev == kEmpty || prev == key) {
+                atomicMin(slot_pos + h, (int32_t)t);
                 slot = (int32_t)h;
                 break;
             }
@@ -94,15 +95,90 @@ __global__ void k_fiber_insert(FiberKeyArgs f, int64_t nnz, unsigned long long *
     }
 }
 
-__global__ void k_fiber_number(const unsigned long long *table, const int32_t *slot_pos,
-                               int64_t cap, int32_t *slot_fid, int32_t *rep,
-                               unsigned long long *count) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (table[i] == kEmpty) continue;
-        const unsigned long long id = atomicAdd(count, 1ull);
-        slot_fid[i] = (int32_t)id;
-        rep[id] = slot_pos[i];
+// Numbering in the order of first positions.  A position is a representative
+// when it is its fiber's first position; kScanBlock positions per block.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ bool is_rep(const int32_t *slot_of, const int32_t *slot_pos, int64_t t,
+                                       int64_t nnz) {
+    if (t >= nnz) return false;
+    const int32_t s = slot_of[t];
+    return s >= 0 && slot_pos[s] == (int32_t)t;
+}
+
+// counts[b] = representatives among positions [b * kScanBlock, (b + 1) * kScanBlock)
+__global__ void __launch_bounds__(kScanBlock) k_fiber_count(const int32_t *slot_of,
+                                                            const int32_t *slot_pos, int64_t nnz,
+                                                            int32_t *counts) {
+    __shared__ int32_t wsum[kScanBlock / 32];
+    const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const unsigned b = __ballot_sync(kFull, is_rep(slot_of, slot_pos, t, nnz));
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t c = 0;
+        for (int w = 0; w < kScanBlock / 32; ++w) c += wsum[w];
+        counts[blockIdx.x] = c;
+    }
+}
+
+// Exclusive prefix sums of the block counts (one block, in place), and the
+// total into *count.
+__global__ void __launch_bounds__(1024) k_fiber_scan(int32_t *counts, int64_t nblocks,
+                                                     unsigned long long *count) {
+    __shared__ long long carry;
+    __shared__ int32_t wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nblocks; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < nblocks ? counts[i] : 0;
+        // inclusive scan inside the warp, then across warps
+        int32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, x, d);
+            if ((threadIdx.x & 31) >= d) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int32_t w = wsum[threadIdx.x];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, w, d);
+                if ((int)threadIdx.x >= d) w += y;
+            }
+            wsum[threadIdx.x] = w;
+        }
+        __syncthreads();
+        const int32_t before = (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0) + x - v;
+        if (i < nblocks) counts[i] = (int32_t)(carry + before);
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = (unsigned long long)carry;
+}
+
+// Ids of the representatives: block offset + rank inside the block.
+__global__ void __launch_bounds__(kScanBlock) k_fiber_number(const int32_t *slot_of,
+                                                             const int32_t *slot_pos, int64_t nnz,
+                                                             const int32_t *offsets,
+                                                             int32_t *slot_fid, int32_t *rep) {
+    __shared__ int32_t wsum[kScanBlock / 32];
+    const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const bool r = is_rep(slot_of, slot_pos, t, nnz);
+    const unsigned b = __ballot_sync(kFull, r);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wsum[warp] = __popc(b);
+    __syncthreads();
+    if (r) {
+        int32_t before = offsets[blockIdx.x];
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        before += __popc(b & ((1u << lane) - 1u));
+        slot_fid[slot_of[t]] = before;
+        rep[before] = (int32_t)t;
     }
 }
 
@@ -150,9 +226,31 @@ __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci
 // iteration (f and f + stride: each float4 of B read from shared memory serves
 // both) while the next pair's coordinates and cached rows are in flight;
 // otherwise one fiber per iteration, its coordinates loaded one ahead.
-template <int R, int J, typename CT, int NO>
+// The lane's JL entries of a fiber's v into the table, as float or rounded
+// to bfloat16 (nearest even).
+template <typename VT, int JL>
+__device__ __forceinline__ void store_v(void *V, int64_t off, const float (&vq)[JL]) {
+    if constexpr (sizeof(VT) == 4) {
+        store_run<JL>(static_cast<float *>(V) + off, vq);
+    } else if constexpr (JL == 1) {
+        static_cast<__nv_bfloat16 *>(V)[off] = __float2bfloat16_rn(vq[0]);
+    } else {
+        uint32_t w[JL / 2];
+#pragma unroll
+        for (int q = 0; q < JL / 2; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(vq[2 * q], vq[2 * q + 1]);
+            w[q] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(V) + off;
+        if constexpr (JL == 8) *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        else if constexpr (JL == 4) *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<uint32_t *>(dst) = w[0];
+    }
+}
+
+template <int R, int J, typename CT, int NO, typename VT>
 __global__ void __launch_bounds__(kFibThreads, (NO <= 3 && J <= 16) ? 3 : 1) k_fiber_v(PassArgs a, FiberCoords fc,
-                                                         int64_t nfibers, float *V) {
+                                                         int64_t nfibers, void *V) {
     constexpr int T = R / 4;
     constexpr int JL = J / T;
     constexpr bool PIPE = NO <= 3;
@@ -182,7 +280,7 @@ __global__ void __launch_bounds__(kFibThreads, (NO <= 3 && J <= 16) ? 3 : 1) k_f
         float vq[JL];
 #pragma unroll
         for (int q = 0; q < JL; ++q) vq[q] = vp[q];
-        if (ok) store_run<JL>(V + f * J + sub * JL, vq);
+        if (ok) store_v<VT, JL>(V, f * J + sub * JL, vq);
     };
     if constexpr (PIPE) {
         // two fibers per group and iteration (f and f + stride): every float4 of
@@ -230,8 +328,8 @@ __global__ void __launch_bounds__(kFibThreads, (NO <= 3 && J <= 16) ? 3 : 1) k_f
                 qa[q] = va[q];
                 qb[q] = vb[q];
             }
-            if (oka) store_run<JL>(V + f * J + sub * JL, qa);
-            if (okb) store_run<JL>(V + (f + stride) * J + sub * JL, qb);
+            if (oka) store_v<VT, JL>(V, f * J + sub * JL, qa);
+            if (okb) store_v<VT, JL>(V, (f + stride) * J + sub * JL, qb);
             wa = na;
             wb = nb;
             oka = okna;
@@ -315,14 +413,22 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
     for (int k = 0, q = 0; k < a.N; ++k)
         if (k != a.n) out.c[q++] = fcoord[k];
     const int blocks = sms * 8;
-    k_fiber_clear<<<blocks, kFibThreads, 0, st>>>(table, cap);
+    k_fiber_clear<<<blocks, kFibThreads, 0, st>>>(table, slot_pos, cap);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_fiber_insert<<<blocks, kFibThreads, 0, st>>>(f, a.nnz, table, slot_pos, cap, fid, a.err);
-    k_fiber_number<<<blocks, kFibThreads, 0, st>>>(table, slot_pos, cap, slot_fid, rep, count);
+    // number the fibers in the order of their first positions; the block counts
+    // use the upper half of `rep` (rep needs at most nnz <= cap / 2 entries)
+    const int64_t nb = (a.nnz + kScanBlock - 1) / kScanBlock;
+    int32_t *counts = rep + cap / 2;
+    if (nb > 0) {
+        k_fiber_count<<<(int)nb, kScanBlock, 0, st>>>(fid, slot_pos, a.nnz, counts);
+        k_fiber_scan<<<1, 1024, 0, st>>>(counts, nb, count);
+        k_fiber_number<<<(int)nb, kScanBlock, 0, st>>>(fid, slot_pos, a.nnz, counts, slot_fid, rep);
+    }
     k_fiber_remap<<<blocks, kFibThreads, 0, st>>>(fid, a.nnz, slot_fid);
     k_fiber_coords<<<blocks, kFibThreads, 0, st>>>(f, rep, count, out);
-    *launches += 5;
+    *launches += 7;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     unsigned long long h = 0;
@@ -330,6 +436,12 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     *nfibers = (int64_t)h;
     return e;
+}
+
+// v is stored as bfloat16 when the cached products are (SFT_BF16) and each lane
+// of a T = R/4 group holds at least two entries of a row (J_n >= R/2, J_n >= 8).
+bool fiber_v_bf16(const PassArgs &a, int J, int R) {
+    return a.cbf16 && J >= 8 && J / (R / 4) >= 2;
 }
 
 static FiberCoords fiber_coords(const PassArgs &a, const int32_t *const *fcoord) {
@@ -346,21 +458,28 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
                                  int sms, int64_t *launches) {
     SliceStreams ss = ss_in;
     const cudaStream_t st = ss.tiles;
-    // 1. v of every fiber
+    // 1. v of every fiber (stored as bfloat16 when the cached products are, and
+    // every lane of a group holds at least two entries of a row)
+    const bool vbf16 = fiber_v_bf16(a, J, R);
     if (nfibers > 0) {
         const int64_t per_block = kFibThreads / (R / 4);
         int64_t blocks = (nfibers + per_block - 1) / per_block;
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         const FiberCoords fc = fiber_coords(a, fcoord);
         constexpr int NG = kMaxOrder - 1;
-        if (a.cbf16 && a.N <= 3)
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16, 2><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+        using bf = __nv_bfloat16;
+        if (a.cbf16 && a.N <= 3 && vbf16)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, bf, 2, bf><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+        else if (a.cbf16 && vbf16)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, bf, NG, bf><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+        else if (a.cbf16 && a.N <= 3)
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, bf, 2, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         else if (a.cbf16)
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, __nv_bfloat16, NG><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, bf, NG, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         else if (a.N <= 3)
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, 2><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, 2, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         else
-            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, NG><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
+            SFT_DISPATCH_RJ(R, J, (k_fiber_v<R_, J_, float, NG, float><<<(int)blocks, kFibThreads, 0, st>>>(a, fc, nfibers, V)));
         *launches += 1;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -382,8 +501,9 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.Lseq = Lseq;
     g.Lhead = subslices ? 0 : Lseq;
     g.subslices = subslices ? 1 : 0;
-    // blocked chains: J_n with an MMA shape, and alpha = 1 - lr lambda well away from 0
-    g.gram = (gram && (J == 8 || J == 16 || J == 32) && a.lr * a.lam < 0.5f) ? 1 : 0;
+    // blocked chains: J_n with an MMA shape, alpha = 1 - lr lambda well away from 0,
+    // float32 v
+    g.gram = (gram && !vbf16 && (J == 8 || J == 16 || J == 32) && a.lr * a.lam < 0.5f) ? 1 : 0;
     g.ntiles = (a.nnz + W - 1) / W;
     g.maps = maps;
     g.fid = fid;
@@ -398,7 +518,7 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
                                   sms, launches);
         if (e != cudaSuccess) return e;
     }
-    factor_slices_fv(g, R, J, with_maps, ss, sms, launches);
+    factor_slices_fv(g, R, J, vbf16, with_maps, ss, sms, launches);
     if (fork) {
         cudaEventRecord(ss.chains_done, ss.chains);
         cudaEventRecord(ss.maps_done, ss.maps);

@@ -166,6 +166,48 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src) {
                      : "memory");
 }
 
+// N entries of a v row of type VT (float or bfloat16) from shared memory,
+// widened to float (bfloat16 -> float is exact: the bits are the top half).
+template <typename VT, int N>
+__device__ __forceinline__ void ld_v_smem(const void *src, float (&out)[N]) {
+    if constexpr (sizeof(VT) == 4) {
+        const float *p = static_cast<const float *>(src);
+        if constexpr (N % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < N; q += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(p + q);
+                out[q] = t.x; out[q + 1] = t.y; out[q + 2] = t.z; out[q + 3] = t.w;
+            }
+        } else if constexpr (N == 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p);
+            out[0] = t.x; out[1] = t.y;
+        } else {
+            out[0] = p[0];
+        }
+    } else {
+        const uint32_t *p = static_cast<const uint32_t *>(src);
+        if constexpr (N % 8 == 0) {
+#pragma unroll
+            for (int q = 0; q < N; q += 8) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(p + q / 2);
+                const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    out[q + 2 * k] = __uint_as_float(w[k] << 16);
+                    out[q + 2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+                }
+            }
+        } else if constexpr (N == 4) {
+            const uint2 t = *reinterpret_cast<const uint2 *>(p);
+            out[0] = __uint_as_float(t.x << 16); out[1] = __uint_as_float(t.x & 0xffff0000u);
+            out[2] = __uint_as_float(t.y << 16); out[3] = __uint_as_float(t.y & 0xffff0000u);
+        } else {
+            static_assert(N == 2, "bfloat16 v rows are read at least two entries at a time");
+            out[0] = __uint_as_float(p[0] << 16); out[1] = __uint_as_float(p[0] & 0xffff0000u);
+        }
+    }
+}
+
 struct SliceArgs {
     PassArgs a;              // idx / val in slice order, perm unused
     const int32_t *row_ptr;  // I_n + 1 slice starts
@@ -188,7 +230,8 @@ struct SliceArgs {
     int gram;                // long chains run by the blocked (Gram) kernel
     // fiber-shared v (set for the fiber variant of the factor pass)
     const int32_t *fid;      // fiber of every slice position (-1: bad data)
-    const float *V;          // [nfibers][J]: v = B^(n) p of every fiber
+    const void *V;           // [nfibers][J]: v = B^(n) p of every fiber (float, or bfloat16
+                             // when the context stores v that way; P of the core pass: float)
     int64_t nfibers;
 };
 
@@ -240,7 +283,7 @@ __device__ __forceinline__ void walk_v(const SliceArgs &g, int64_t s0, int64_t s
         }
         if (c.valid && bad) atomicOr(a.err, kErrIndex);
         ok = c.valid && !bad;
-        const float *src = g.V + (int64_t)(ok ? c.f : 0) * J + sub * JL;
+        const float *src = static_cast<const float *>(g.V) + (int64_t)(ok ? c.f : 0) * J + sub * JL;
         if constexpr (JL >= 4) {
 #pragma unroll
             for (int q = 0; q < JL / 4; ++q) {
@@ -307,7 +350,7 @@ struct DeepRing {
 
 constexpr int kDeepP = 16;  // prefetch distance (positions) of the deep walk
 
-template <int R, int J, int P, bool WITH_ROW, typename Body>
+template <int R, int J, int P, bool WITH_ROW, typename VT, typename Body>
 __device__ __forceinline__ void walk_v_deep(const SliceArgs &g, float *ring, int64_t s0,
                                             int64_t s1, int sub, unsigned m, Body &&body) {
     constexpr int T = R / 4;
@@ -331,7 +374,9 @@ __device__ __forceinline__ void walk_v_deep(const SliceArgs &g, float *ring, int
         if (q < n) {
             const int32_t f = fr[fslot];
             if ((uint64_t)(int64_t)f < (uint64_t)g.nfibers)
-                cp_async<JL * 4>(vr + vslot * J + sub * JL, g.V + (int64_t)f * J + sub * JL);
+                cp_async<JL * (int)sizeof(VT)>(
+                    reinterpret_cast<char *>(vr + vslot * J) + sub * JL * sizeof(VT),
+                    static_cast<const char *>(g.V) + ((int64_t)f * J + sub * JL) * sizeof(VT));
         }
     };
     // prologue: scalars of 0 .. P-1 (landed before anything else), then the v
@@ -356,17 +401,7 @@ __device__ __forceinline__ void walk_v_deep(const SliceArgs &g, float *ring, int
         const float x = xr[ss];
         int32_t row = WITH_ROW ? rr[ss] : -1;
         float vq[JL];
-        const float *src = vr + vs * J + sub * JL;
-        if constexpr (JL >= 4) {
-#pragma unroll
-            for (int q = 0; q < JL; q += 4) {
-                const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
-                vq[q] = t4.x; vq[q + 1] = t4.y; vq[q + 2] = t4.z; vq[q + 3] = t4.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < JL; ++q) vq[q] = src[q];
-        }
+        ld_v_smem<VT, JL>(reinterpret_cast<const char *>(vr + vs * J) + sub * JL * sizeof(VT), vq);
         if constexpr (WITH_ROW) {
             // a coordinate P positions ahead that starts a new slice: bring its
             // factor row towards the SM (L2) before the walk switches to it
@@ -410,7 +445,7 @@ __device__ __forceinline__ void walk_steps(const SliceArgs &g, const float *sB, 
     constexpr int JL = J / (R / 4);
     if constexpr (FV) {
         if (deep)
-            walk_v_deep<R, J, kDeepP, WITH_ROW>(g, deep, s0, s1, sub, m, step);
+            walk_v_deep<R, J, kDeepP, WITH_ROW, CT>(g, deep, s0, s1, sub, m, step);
         else
             walk_v<R, J, DMAX, WITH_ROW>(g, s0, s1, sub, step);
     } else {
@@ -648,7 +683,7 @@ constexpr int kLaneTileP = 8;     // ... of a tile walk (its slots also hold row
 // position's v (J floats); with ROWS, row = its mode-n coordinate and newrow =
 // the pass-start value of that row's factor row (valid where the coordinate
 // differs from the previous position's).
-template <int J, int P, bool ROWS, typename Body>
+template <int J, int P, bool ROWS, typename VT, typename Body>
 __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64_t s0, int64_t s1,
                                           Body &&body) {
     using LR = LaneRing<J, P, ROWS>;
@@ -676,7 +711,10 @@ __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64
     auto vcopy = [&](int q, int fslot, int vslot) {
         if (q < n) {
             const int32_t f = fr[fslot];
-            if ((uint32_t)f < nf) cp_async<J * 4>(vr + vslot * VW, g.V + (int64_t)f * J);
+            if ((uint32_t)f < nf)
+                cp_async<J * (int)sizeof(VT)>(vr + vslot * VW,
+                                              static_cast<const char *>(g.V) +
+                                                  (int64_t)f * J * (int64_t)sizeof(VT));
             if constexpr (ROWS) {
                 const int32_t r = rr[fslot];
                 if (r != last_row && (uint32_t)r < In)
@@ -691,11 +729,7 @@ __device__ __forceinline__ void walk_lane(const SliceArgs &g, float *ring, int64
         int32_t row = ROWS ? rr[ss] : -1;
         float v[J];
         const float *src = vr + vs * VW;
-#pragma unroll
-        for (int q = 0; q < J; q += 4) {
-            const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
-            v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
-        }
+        ld_v_smem<VT, J>(src, v);
         bool ok = (uint32_t)f < nf;
         if (ROWS && (uint32_t)row >= In) {
             ok = false;
@@ -761,7 +795,7 @@ __device__ __forceinline__ void lane_step(const PassArgs &a, float (&av)[J], con
 
 // Crossing slices (whole, or the head of a long slice), one per lane; list
 // entry c goes to block c % gridDim.x so that a short list spreads over the SMs.
-template <int R, int J>
+template <int R, int J, typename VT>
 __global__ void __launch_bounds__(kLaneThreads) k_slices_chains1(SliceArgs g) {
     constexpr int T = R / 4;
     using LR = LaneRing<J, kLaneChainP, false>;
@@ -779,7 +813,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_slices_chains1(SliceArgs g) {
         float *arow = a.A + (int64_t)r * J;
         float av[J];
         load_run<J>(arow, av);
-        walk_lane<J, kLaneChainP, false>(g, ring, s, e1,
+        walk_lane<J, kLaneChainP, false, VT>(g, ring, s, e1,
                                          [&](int32_t, float x, bool ok, const float (&v)[J],
                                              const float *) { lane_step<T, J>(a, av, v, x, ok); });
         store_run<J>(arow, av);
@@ -789,7 +823,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_slices_chains1(SliceArgs g) {
 // Slices inside tiles, one tile per lane (the same bounds as k_slices_tiles);
 // the factor row of each new slice is staged in the ring with the position that
 // starts it.
-template <int R, int J>
+template <int R, int J, typename VT>
 __global__ void __launch_bounds__(kLaneThreads) k_slices_tiles1(SliceArgs g) {
     constexpr int T = R / 4;
     using LR = LaneRing<J, kLaneTileP, true>;
@@ -825,7 +859,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_slices_tiles1(SliceArgs g) {
         float av[J];
 #pragma unroll
         for (int q = 0; q < J; ++q) av[q] = 0.f;
-        walk_lane<J, kLaneTileP, true>(g, ring, q0, q1,
+        walk_lane<J, kLaneTileP, true, VT>(g, ring, q0, q1,
                                        [&](int32_t row, float x, bool ok, const float (&v)[J],
                                            const float *newrow) {
             if (row != cur) {  // the slice changes: write the finished row, take the next
@@ -1008,7 +1042,7 @@ __global__ void __launch_bounds__(kGramWarps * 32) k_slices_gram(SliceArgs g) {
             float *dst = vbuf + (b % NVB) * 32 * SV + lane * SV;
             const int32_t f = p < n ? fbuf[(b % NFB) * 32 + lane] : -1;
             if (p < n && (uint32_t)f < nf) {
-                cp_async<J * 4>(dst, g.V + (int64_t)f * J);
+                cp_async<J * 4>(dst, static_cast<const float *>(g.V) + (int64_t)f * J);
                 cp_async<4>(xbuf + (b % NVB) * 32 + lane, val + p);
             } else {
 #pragma unroll
@@ -1166,7 +1200,7 @@ struct MapRing {
 
 // Calls step(v, vl, x, ok) for slice positions [s0, s1) in order: v = all J
 // entries of the position's fiber v (shared memory), vl = the lane's J/T.
-template <int R, int J, typename Step>
+template <int R, int J, typename VT, typename Step>
 __device__ __forceinline__ void walk_v_ring(const SliceArgs &g, float *ring, int64_t s0, int64_t s1,
                                             int sub, unsigned m, Step &&step) {
     constexpr int T = R / 4;
@@ -1184,7 +1218,10 @@ __device__ __forceinline__ void walk_v_ring(const SliceArgs &g, float *ring, int
         if (valid && !good) atomicOr(a.err, kErrIndex);
         const int slot = (int)(q % D);
         okm = (okm & ~(1u << slot)) | ((valid && good) ? (1u << slot) : 0u);
-        if (valid && good) cp_async<JL * 4>(ring + slot * J + sub * JL, g.V + (int64_t)f * J + sub * JL);
+        if (valid && good)
+            cp_async<JL * (int)sizeof(VT)>(
+                reinterpret_cast<char *>(ring + slot * J) + sub * JL * sizeof(VT),
+                static_cast<const char *>(g.V) + ((int64_t)f * J + sub * JL) * sizeof(VT));
         cp_async_commit();
     };
     auto ld_fid = [&](int64_t q) { return q < n ? __ldg(g.fid + s0 + q) : -1; };
@@ -1213,13 +1250,8 @@ __device__ __forceinline__ void walk_v_ring(const SliceArgs &g, float *ring, int
                 fr[sq] = ld_fid(i + P + D);
                 float v[J], vl[JL];
                 const float *src = ring + u * J;  // slot i % D == u (b is a multiple of D)
-#pragma unroll
-                for (int q = 0; q < J; q += 4) {
-                    const float4 t4 = *reinterpret_cast<const float4 *>(src + q);
-                    v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
-                }
-#pragma unroll
-                for (int q = 0; q < JL; ++q) vl[q] = src[sub * JL + q];
+                ld_v_smem<VT, J>(src, v);
+                ld_v_smem<VT, JL>(reinterpret_cast<const char *>(src) + sub * JL * sizeof(VT), vl);
                 const float x = xr[u];
                 const bool ok = (okm >> u) & 1u;
                 xr[u] = ld_x(i + D);
@@ -1343,7 +1375,7 @@ __device__ __forceinline__ void compose_map(const SliceArgs &g, const float *sB,
         }
     };
     if constexpr (FV && MapRing<R, J>::use) {
-        walk_v_ring<R, J>(g, ring, s0, s1, sub, m, apply);
+        walk_v_ring<R, J, CT>(g, ring, s0, s1, sub, m, apply);
     } else {
         // One-step software pipeline: v of position t (independent of M) is
         // computed while the rank-1 update of position t-1 is applied.
@@ -1637,13 +1669,15 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
     if constexpr (FV && lane_kernels<R, J>()) {
         constexpr size_t csm = (size_t)kLaneThreads * LaneRing<J, kLaneChainP, false>::words * 4;
         constexpr size_t tsm = (size_t)kLaneThreads * LaneRing<J, kLaneTileP, true>::words * 4;
-        cudaFuncSetAttribute(k_slices_chains1<R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_slices_chains1<R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)csm);
-        cudaFuncSetAttribute(k_slices_tiles1<R, J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_slices_tiles1<R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tsm);
+        // blocked chains exist only if a chain may reach kGramMin positions
+        const bool gram = g.gram && g.Lseq >= kGramMin;
         if (g.ntiles > 1) {
             if constexpr (J == 8 || J == 16 || J == 32) {
-                if (g.gram) {
+                if (gram) {
                     // the blocked chains first, on their own stream: they are the
                     // longest dependent sequences of the pass
                     cudaFuncSetAttribute(k_slices_gram<J>,
@@ -1655,14 +1689,14 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
                     *launches += 1;
                 }
             }
-            const int gch = grid_for(k_slices_chains1<R, J>, kLaneThreads, csm, kLaneThreads,
+            const int gch = grid_for(k_slices_chains1<R, J, CT>, kLaneThreads, csm, kLaneThreads,
                                      g.ntiles - 1, sms);
-            k_slices_chains1<R, J><<<gch, kLaneThreads, csm, g.gram ? ss.tiles : ss.chains>>>(g);
+            k_slices_chains1<R, J, CT><<<gch, kLaneThreads, csm, gram ? ss.tiles : ss.chains>>>(g);
             *launches += 1;
         }
-        const int gd = grid_for(k_slices_tiles1<R, J>, kLaneThreads, tsm, kLaneThreads, g.ntiles,
+        const int gd = grid_for(k_slices_tiles1<R, J, CT>, kLaneThreads, tsm, kLaneThreads, g.ntiles,
                                 sms);
-        k_slices_tiles1<R, J><<<gd, kLaneThreads, tsm, ss.tiles>>>(g);
+        k_slices_tiles1<R, J, CT><<<gd, kLaneThreads, tsm, ss.tiles>>>(g);
         *launches += 1;
         return;
     }
@@ -1723,8 +1757,10 @@ cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int 
 cudaError_t launch_piece_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
                               int64_t *launches);
 // fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
-void factor_slices_fv(const SliceArgs &g, int R, int J, bool with_maps, const SliceStreams &ss,
-                      int sms, int64_t *launches);
+void factor_slices_fv(const SliceArgs &g, int R, int J, bool vbf16, bool with_maps,
+                      const SliceStreams &ss, int sms, int64_t *launches);
+void factor_slices_fv_bf16(const SliceArgs &g, int R, int J, bool with_maps,
+                           const SliceStreams &ss, int sms, int64_t *launches);
 int core_slices_fv(const SliceArgs &g, int R, int J, float *partials, int max_blocks,
                    cudaStream_t st, int sms);
 

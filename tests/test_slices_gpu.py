@@ -341,17 +341,22 @@ def test_bf16_refresh_and_predictions(sft, oracle_mod):
           f"worst |x^ err|/scale = {float(np.max(np.abs(xh - ref.predict(ix)) / scale)):.3e}")
 
 
-def test_bf16_slice_passes(sft, oracle_mod):
+@pytest.mark.parametrize("fibers", [False, True])
+def test_bf16_slice_passes(sft, oracle_mod, fibers):
     """One factor pass (element by element) and one whole-pass core step per mode
-    with bfloat16 cached products track the float64 oracle within 2e-2."""
+    with bfloat16 cached products track the float64 oracle within 2e-2; with
+    fibers the v table itself is stored in bfloat16."""
     T = small_tensor()
     idx, val = to_dev(T)
     ix = np_idx(T.idx)
     dec = sft.Decomposition(T.A0, T.B0, prec=sft.SFT_BF16)
+    dec.set_slice_tiling(64, 128)  # heads, maps and chains all in use
     ref = oracle_mod.Model([a.numpy() for a in T.A0], [b.numpy() for b in T.B0])
     for n in range(3):
         A0 = dec.A[n].cpu().numpy().astype(np.float64)
         sl = dec.slices(n, idx, val, None)
+        if fibers:
+            sl.build_fibers(dec)
         dec.update_factors_slices(sl, lr=0.05, lam=0.01)
         dec.refresh(n)
         S1, S2 = ref.factor_pass_scaled(n, ix, T.val.numpy(), batch=1, lr=0.05, lam=0.01)
@@ -461,6 +466,12 @@ def test_fiber_pass_equals_row_pass(sft, case):
         dec.sync(60_000)
         outs.append([a.clone() for a in dec.A])
     for n, (a, b) in enumerate(zip(*outs)):
+        if case == "bf16":
+            # with bfloat16 cached products the fiber table stores v rounded to
+            # bfloat16 (the per-nonzero path keeps v in float32): one bfloat16
+            # rounding of v apart, far inside the 2e-2 bfloat16 bound
+            assert rel_fro(b.cpu().numpy(), a.cpu().numpy()) < 2e-3, (case, n)
+            continue
         assert torch.equal(a, b), (case, n, (a - b).abs().max().item())
 
 
