@@ -455,8 +455,6 @@ def run_batch(args, world, rank, lr):
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
-            "e2e_raw": e2e_raw,
-            "precision_and_convergence": conv,
             "cpu_baseline": cpu,
         }))
     if world > 1:
@@ -645,8 +643,6 @@ def run_autograd(args, world, rank, sft, T, spec, metric, unit, gen_s):
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
-            "e2e_raw": e2e_raw,
-            "precision_and_convergence": conv,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
