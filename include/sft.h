@@ -217,8 +217,8 @@ size_t sft_slices_workspace_bytes(const sft_ctx *ctx, int32_t mode, int64_t nnz)
  * order that built the layout (slices of one mode never interact during a
  * factor pass).  Long slices are cut into tile-sized pieces composed as affine
  * maps and applied in order (same recurrence, re-associated).  Deterministic:
- * the only atomic collects the list of slices run whole, whose order affects
- * no result.  workspace: device buffer of sft_slices_workspace_bytes bytes
+ * the only atomics collect the lists of slices, tile interiors and map pieces
+ * to run, whose order affects no result.  workspace: device buffer of sft_slices_workspace_bytes bytes
  * (the piece maps and that list).  Enqueues only. */
 sft_status sft_update_factors_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *sidx,
                                      const float *sval, const int32_t *row_ptr, int64_t nnz,

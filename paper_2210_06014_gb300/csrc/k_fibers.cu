@@ -511,8 +511,10 @@ cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int6
     g.nfibers = nfibers;
     const bool with_maps = maps != nullptr;
     {
+        // with the one-lane kernel (J_n <= 16) the chain list keeps only the
+        // blocked chains; the lane kernel builds its own sorted work list
         cudaError_t e = launch_chain_list(g, (char *)maps + slice_chain_list_offset(g.ntiles, J),
-                                          ss.chains, sms, launches);
+                                          slice_lane_kernels(J), ss.chains, sms, launches);
         if (e == cudaSuccess && with_maps && !subslices)
             e = launch_piece_list(g, (char *)maps + slice_piece_list_offset(g.ntiles, J), ss.maps,
                                   sms, launches);

@@ -476,27 +476,26 @@ int slice_core_tile_length(int64_t nnz, int sms) {
 // (Lhead > 0), every longer crossing slice too (for its head).  A chain of at
 // least gram_min positions (gram_min > 0) is stored from the back of the list
 // (count[1]) for the blocked-chain kernel, shorter ones from the front
-// (count[0]); the list has room for `cap` entries (one per tile boundary).
+// (count[0]) unless gram_only (the one-lane kernel takes them from its own
+// work list); the list has room for `cap` entries (one per tile boundary).
 __global__ void k_chain_list(const int32_t *__restrict__ row_ptr, int32_t In, int64_t W,
                              int64_t Lseq, int64_t Lhead, int64_t nnz, int64_t gram_min,
-                             int64_t cap, int32_t *list, unsigned int *count) {
+                             int gram_only, int64_t cap, int32_t *list, unsigned int *count) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < In;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = row_ptr[r], e = row_ptr[r + 1];
-        if (Lseq <= 0 || s < 0 || s >= e || e > nnz) continue;
-        if (e - s > Lseq && Lhead <= 0) continue;
-        if (s / W == (e - 1) / W) continue;  // inside one tile: the tile kernel runs it
-        const int64_t run = e - s <= Lseq ? e - s : Lhead;
-        if (gram_min > 0 && run >= gram_min)
+        bool gram;
+        const int64_t run = chain_run(row_ptr, (int32_t)r, W, Lseq, Lhead, nnz, gram_min, &gram);
+        if (run <= 0) continue;
+        if (gram)
             list[cap - 1 - atomicAdd(&count[1], 1u)] = (int32_t)r;
-        else
+        else if (!gram_only)
             list[atomicAdd(&count[0], 1u)] = (int32_t)r;
     }
 }
 
 // list_ws: 16 bytes of counts, then room for one row per tile boundary.
-cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
-                              int64_t *launches) {
+cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, bool gram_only, cudaStream_t st,
+                              int sms, int64_t *launches) {
     g.nchains = (unsigned int *)list_ws;
     g.chains = (int32_t *)((char *)list_ws + 16);
     cudaError_t e = cudaMemsetAsync(g.nchains, 0, 2 * sizeof(unsigned int), st);
@@ -506,9 +505,124 @@ cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int 
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
     if (blocks < 1) blocks = 1;
     k_chain_list<<<(int)blocks, 256, 0, st>>>(g.row_ptr, In, g.W, g.Lseq, g.Lhead, g.a.nnz,
-                                               g.gram ? kGramMin : 0,
+                                               g.gram ? kGramMin : 0, gram_only ? 1 : 0,
                                                g.ntiles < 1 ? 1 : g.ntiles, g.chains, g.nchains);
     *launches += 1;
+    return cudaGetLastError();
+}
+
+// The one-lane kernel's work list, sorted by length: the interiors of the
+// tiles and the chains below the blocked kernel's threshold, as item * 2 +
+// kind, grouped by length class (longest first; order within a class
+// arbitrary: every item writes only its own rows, so the order affects no
+// result).  Item k of the enumeration: k < ntiles is tile k, else row
+// k - ntiles.
+__device__ __forceinline__ int64_t lane_item_len(const SliceArgs &g, int64_t k, int64_t gram_min,
+                                                 uint32_t *item) {
+    if (k < g.ntiles) {
+        int64_t q0, q1;
+        if (!tile_inner(g, k, q0, q1)) {
+            atomicOr(g.a.err, kErrIndex);
+            return 0;
+        }
+        *item = (uint32_t)(k << 1);
+        return q1 - q0;
+    }
+    const int64_t r = k - g.ntiles;
+    bool gram;
+    const int64_t run = chain_run(g.row_ptr, (int32_t)r, g.W, g.Lseq, g.Lhead, g.a.nnz, gram_min,
+                                  &gram);
+    *item = (uint32_t)((r << 1) | 1);
+    return gram ? 0 : run;
+}
+
+constexpr int kLaneListThreads = 256;
+
+// Pass 1: items per length class (block histograms, added to lane_cnt[0..]).
+__global__ void __launch_bounds__(kLaneListThreads) k_lane_count(SliceArgs g, int64_t gram_min) {
+    __shared__ unsigned int h[kLaneBuckets];
+    for (int b = threadIdx.x; b < kLaneBuckets; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const int64_t n = g.ntiles + g.a.dims[g.a.n];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t item;
+        const int64_t len = lane_item_len(g, k, gram_min, &item);
+        if (len > 0) atomicAdd(&h[lane_bucket(len)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kLaneBuckets; b += blockDim.x)
+        if (h[b]) atomicAdd(&g.lane_cnt[b], h[b]);
+}
+
+// Pass 2: every block counts its own items per class again, reserves a range
+// of each class from the cursors (lane_cnt[kLaneBuckets + b]), and places its
+// items in it.  The class starts are the prefix sums of the pass-1 counts.
+__global__ void __launch_bounds__(kLaneListThreads) k_lane_scatter(SliceArgs g, int64_t gram_min) {
+    __shared__ unsigned int start[kLaneBuckets];  // class starts, then this block's range starts
+    __shared__ unsigned int h[kLaneBuckets];
+    if (threadIdx.x < 32) {  // exclusive prefix sum of the class counts, 4 classes per lane
+        unsigned int c[kLaneBuckets / 32], run = 0;
+#pragma unroll
+        for (int i = 0; i < kLaneBuckets / 32; ++i) {
+            c[i] = g.lane_cnt[threadIdx.x * (kLaneBuckets / 32) + i];
+            run += c[i];
+        }
+        unsigned int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)threadIdx.x >= o) incl += y;
+        }
+        unsigned int off = incl - run;
+#pragma unroll
+        for (int i = 0; i < kLaneBuckets / 32; ++i) {
+            start[threadIdx.x * (kLaneBuckets / 32) + i] = off;
+            off += c[i];
+        }
+    }
+    for (int b = threadIdx.x; b < kLaneBuckets; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const int64_t n = g.ntiles + g.a.dims[g.a.n];
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = k0; k < n; k += stride) {
+        uint32_t item;
+        const int64_t len = lane_item_len(g, k, gram_min, &item);
+        if (len > 0) atomicAdd(&h[lane_bucket(len)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kLaneBuckets; b += blockDim.x) {
+        const unsigned int mine = h[b];
+        start[b] += mine ? atomicAdd(&g.lane_cnt[kLaneBuckets + b], mine) : 0u;
+        h[b] = 0;
+    }
+    __syncthreads();
+    for (int64_t k = k0; k < n; k += stride) {
+        uint32_t item;
+        const int64_t len = lane_item_len(g, k, gram_min, &item);
+        if (len <= 0) continue;
+        const int b = lane_bucket(len);
+        g.lane_items[start[b] + atomicAdd(&h[b], 1u)] = item;
+    }
+}
+
+// list_ws: the class counts, cursors and grab counter (2 kLaneBuckets + 4
+// words), then room for one item per tile and one per row of the mode.
+cudaError_t launch_lane_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                             int64_t *launches) {
+    g.lane_cnt = (unsigned int *)list_ws;
+    g.lane_items = (uint32_t *)((char *)list_ws + (2 * kLaneBuckets + 4) * sizeof(unsigned int));
+    cudaError_t e = cudaMemsetAsync(g.lane_cnt, 0, (2 * kLaneBuckets + 4) * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const int64_t n = g.ntiles + g.a.dims[g.a.n];
+    int64_t blocks = (n + kLaneListThreads - 1) / kLaneListThreads;
+    if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+    if (blocks < 1) blocks = 1;
+    const int64_t gram_min = g.gram ? kGramMin : 0;
+    k_lane_count<<<(int)blocks, kLaneListThreads, 0, st>>>(g, gram_min);
+    k_lane_scatter<<<(int)blocks, kLaneListThreads, 0, st>>>(g, gram_min);
+    *launches += 2;
     return cudaGetLastError();
 }
 
@@ -517,8 +631,9 @@ size_t slice_maps_bytes(int64_t ntiles, int J) {
 }
 
 // Workspace of a slice factor pass: the piece maps, the chain list (a count
-// and one row per tile), then the piece list (two counts and two entries per
-// tile), each part starting on a 16-byte boundary.
+// and one row per tile), the piece list (two counts and two entries per
+// tile), then the one-lane work list, each part starting on a 16-byte
+// boundary.
 size_t slice_chain_list_offset(int64_t ntiles, int J) { return slice_maps_bytes(ntiles, J); }
 
 size_t slice_piece_list_offset(int64_t ntiles, int J) {
@@ -526,8 +641,15 @@ size_t slice_piece_list_offset(int64_t ntiles, int J) {
     return (o + 15) / 16 * 16;
 }
 
-size_t slice_workspace_total(int64_t ntiles, int J) {
-    return slice_piece_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * 4;
+size_t slice_lane_list_offset(int64_t ntiles, int J) {
+    const size_t o = slice_piece_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * 4;
+    return (o + 15) / 16 * 16;
+}
+
+// The lane list needs the mode's length I_n too (one item per row at most).
+size_t slice_workspace_total(int64_t ntiles, int J, int64_t In) {
+    return slice_lane_list_offset(ntiles, J) + (2 * kLaneBuckets + 4) * sizeof(unsigned int) +
+           (size_t)((ntiles < 1 ? 1 : ntiles) + (In < 0 ? 0 : In)) * 4;
 }
 
 // The pass's map pieces into the piece list: full-tile pieces from the front,
@@ -599,7 +721,7 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
     const bool with_maps = maps != nullptr;
     {
         cudaError_t e = launch_chain_list(g, (char *)maps + slice_chain_list_offset(g.ntiles, J),
-                                          ss.chains, sms, launches);
+                                          false, ss.chains, sms, launches);
         if (e == cudaSuccess && with_maps && !subslices)
             e = launch_piece_list(g, (char *)maps + slice_piece_list_offset(g.ntiles, J), ss.maps,
                                   sms, launches);

@@ -538,8 +538,9 @@ size_t sft_slices_workspace_bytes(const sft_ctx *c, int32_t mode, int64_t nnz) {
     if (!c || mode < 0 || mode >= c->N || nnz < 0) return 0;
     const int64_t W = slice_W(c, nnz);
     const int64_t ntiles = (nnz + W - 1) / W;
-    // the piece maps, the pass's chain list and its piece list
-    return slice_workspace_total(ntiles, c->J[mode]);
+    // the piece maps, the pass's chain list, its piece list and its one-lane
+    // work list
+    return slice_workspace_total(ntiles, c->J[mode], c->dims[mode]);
 }
 
 static sft_status check_slices(sft_ctx *c, int32_t mode, const int32_t *const *sidx,

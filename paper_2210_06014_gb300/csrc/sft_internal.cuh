@@ -85,7 +85,11 @@ int64_t slice_sort_length(int64_t nnz);
 size_t slice_maps_bytes(int64_t ntiles, int J);
 size_t slice_chain_list_offset(int64_t ntiles, int J);
 size_t slice_piece_list_offset(int64_t ntiles, int J);
-size_t slice_workspace_total(int64_t ntiles, int J);
+size_t slice_lane_list_offset(int64_t ntiles, int J);
+size_t slice_workspace_total(int64_t ntiles, int J, int64_t In);
+// the fiber factor pass runs its tiles and short chains with the one-lane
+// kernel (k_slices_lanes) when J_n <= 16
+constexpr bool slice_lane_kernels(int J) { return J <= 16; }
 int slice_tile_length(int64_t nnz, int sms);
 int slice_core_tile_length(int64_t nnz, int sms);
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,

@@ -16,12 +16,13 @@
 #ifndef SFT_MAP_RING_D
 #define SFT_MAP_RING_D 4
 #endif
-// one-lane chains: prefetch distance and packed partial sums of a . v
-#ifndef SFT_LANE_CHAIN_P
-#define SFT_LANE_CHAIN_P 16
-#endif
+// one-lane walks: packed partial sums of a . v
 #ifndef SFT_LANE_DOT_PACKED
 #define SFT_LANE_DOT_PACKED 1
+#endif
+// prefetch distance (positions) of the one-lane walks of the sorted work list
+#ifndef SFT_LANE_P
+#define SFT_LANE_P 8
 #endif
 
 namespace sft {
@@ -228,6 +229,11 @@ struct SliceArgs {
     int32_t *chains;         // their rows, in no particular order (blocked chains from the back)
     unsigned int *nchains;   // [0]: chains for the lane kernels, [1]: for the blocked kernel
     int gram;                // long chains run by the blocked (Gram) kernel
+    // work list of the one-lane kernel (built per pass by k_lane_count /
+    // k_lane_scatter): tile interiors and chains, longest first
+    uint32_t *lane_items;    // item * 2 + kind (0: interior of tile item, 1: chain of row item)
+    unsigned int *lane_cnt;  // [kLaneBuckets] items per length class, [kLaneBuckets] scatter
+                             // cursors, then the grab counter
     // fiber-shared v (set for the fiber variant of the factor pass)
     const int32_t *fid;      // fiber of every slice position (-1: bad data)
     const void *V;           // [nfibers][J]: v = B^(n) p of every fiber (float, or bfloat16
@@ -676,8 +682,6 @@ struct LaneRing {
 };
 
 constexpr int kLaneThreads = 64;  // block size of the one-lane kernels
-constexpr int kLaneChainP = SFT_LANE_CHAIN_P;  // prefetch distance of a chain
-constexpr int kLaneTileP = 8;     // ... of a tile walk (its slots also hold rows)
 
 // Calls body(row, x, ok, v, newrow) for positions [s0, s1) in order: v = the
 // position's v (J floats); with ROWS, row = its mode-n coordinate and newrow =
@@ -793,75 +797,119 @@ __device__ __forceinline__ void lane_step(const PassArgs &a, float (&av)[J], con
     }
 }
 
-// Crossing slices (whole, or the head of a long slice), one per lane; list
-// entry c goes to block c % gridDim.x so that a short list spreads over the SMs.
-template <int R, int J, typename VT>
-__global__ void __launch_bounds__(kLaneThreads) k_slices_chains1(SliceArgs g) {
-    constexpr int T = R / 4;
-    using LR = LaneRing<J, kLaneChainP, false>;
-    extern __shared__ __align__(16) float lane_ring[];
-    float *ring = lane_ring + threadIdx.x * LR::words;
+// The interior [q0, q1) of tile t: its positions minus the slices that cross
+// either of its boundaries (those run as chains or through maps).  False on a
+// slice layout that contradicts the coordinates (the caller flags it).
+__device__ __forceinline__ bool tile_inner(const SliceArgs &g, int64_t t, int64_t &q0,
+                                           int64_t &q1) {
     const PassArgs &a = g.a;
-    const int64_t n = (int64_t)*g.nchains;
-    const int64_t lanes = (int64_t)gridDim.x * kLaneThreads;
-    for (int64_t c = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; c < n; c += lanes) {
-        const int32_t r = __ldg(g.chains + c);
-        if ((uint32_t)r >= (uint32_t)a.dims[a.n]) continue;
-        const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
-        if (!slice_ok(g, s, e)) continue;
-        const int64_t e1 = e - s <= g.Lseq ? e : min(e, s + g.Lhead);
-        float *arow = a.A + (int64_t)r * J;
-        float av[J];
-        load_run<J>(arow, av);
-        walk_lane<J, kLaneChainP, false, VT>(g, ring, s, e1,
-                                         [&](int32_t, float x, bool ok, const float (&v)[J],
-                                             const float *) { lane_step<T, J>(a, av, v, x, ok); });
-        store_run<J>(arow, av);
-    }
-}
-
-// Slices inside tiles, one tile per lane (the same bounds as k_slices_tiles);
-// the factor row of each new slice is staged in the ring with the position that
-// starts it.
-template <int R, int J, typename VT>
-__global__ void __launch_bounds__(kLaneThreads) k_slices_tiles1(SliceArgs g) {
-    constexpr int T = R / 4;
-    using LR = LaneRing<J, kLaneTileP, true>;
-    extern __shared__ __align__(16) float lane_ring[];
-    float *ring = lane_ring + threadIdx.x * LR::words;
-    const PassArgs &a = g.a;
-    const int64_t lanes = (int64_t)gridDim.x * kLaneThreads;
     const int32_t *rowidx = a.idx[a.n];
     const uint32_t In = (uint32_t)a.dims[a.n];
-    for (int64_t t = (int64_t)blockIdx.x * kLaneThreads + threadIdx.x; t < g.ntiles; t += lanes) {
-        const int64_t p0 = t * g.W;
-        const int64_t p1 = min(a.nnz, p0 + g.W);
-        int64_t q0 = p0, q1 = p1;
-        bool bad = false;
-        const int32_t r0 = __ldg(rowidx + p0);
-        if (p0 > 0 && (uint32_t)r0 < In && __ldg(rowidx + p0 - 1) == r0) {
-            const int64_t e0 = __ldg(g.row_ptr + r0 + 1);
-            if (e0 <= p0 || e0 > a.nnz) bad = true;
-            else q0 = min(e0, p1);
-        }
-        const int32_t r1 = __ldg(rowidx + p1 - 1);
-        if (p1 < a.nnz && (uint32_t)r1 < In && __ldg(rowidx + p1) == r1) {
-            const int64_t s1 = __ldg(g.row_ptr + r1);
-            if (s1 < 0 || s1 > p1 - 1) bad = true;
-            else q1 = max(s1, q0);
-        }
-        if (bad) {
-            atomicOr(a.err, kErrIndex);
-            continue;
-        }
-        if (q0 >= q1) continue;
+    const int64_t p0 = t * g.W;
+    const int64_t p1 = min(a.nnz, p0 + g.W);
+    q0 = p0;
+    q1 = p1;
+    const int32_t r0 = __ldg(rowidx + p0);
+    if (p0 > 0 && (uint32_t)r0 < In && __ldg(rowidx + p0 - 1) == r0) {
+        const int64_t e0 = __ldg(g.row_ptr + r0 + 1);
+        if (e0 <= p0 || e0 > a.nnz) return false;
+        q0 = min(e0, p1);
+    }
+    const int32_t r1 = __ldg(rowidx + p1 - 1);
+    if (p1 < a.nnz && (uint32_t)r1 < In && __ldg(rowidx + p1) == r1) {
+        const int64_t s1 = __ldg(g.row_ptr + r1);
+        if (s1 < 0 || s1 > p1 - 1) return false;
+        q1 = max(s1, q0);
+    }
+    return true;
+}
+
+// The part of row r's slice that runs as one element-by-element chain: the
+// whole slice if it crosses a tile boundary and has at most Lseq nonzeros, its
+// first Lhead nonzeros if it is longer (and long slices have heads); else
+// none (run = 0).  gram_min > 0: chains of at least gram_min positions belong
+// to the blocked kernel and are left out too.
+__device__ __forceinline__ int64_t chain_run(const int32_t *row_ptr, int32_t r, int64_t W,
+                                             int64_t Lseq, int64_t Lhead, int64_t nnz,
+                                             int64_t gram_min, bool *gram) {
+    const int64_t s = row_ptr[r], e = row_ptr[r + 1];
+    *gram = false;
+    if (Lseq <= 0 || s < 0 || s >= e || e > nnz) return 0;
+    if (e - s > Lseq && Lhead <= 0) return 0;
+    if (s / W == (e - 1) / W) return 0;  // inside one tile: the tile's interior
+    const int64_t run = e - s <= Lseq ? e - s : Lhead;
+    *gram = gram_min > 0 && run >= gram_min;
+    return run;
+}
+
+// Length class of a work item, longest first: 4 classes per octave (class
+// 4 floor(log2 len) + the two bits after the leading one), reversed.
+constexpr int kLaneBuckets = 128;
+__device__ __forceinline__ int lane_bucket(int64_t len) {
+    const uint64_t u = (uint64_t)len;
+    const int lz = 63 - __clzll(u);
+    const int q = lz >= 2 ? (int)((u >> (lz - 2)) & 3u) : (int)((u << (2 - lz)) & 3u);
+    const int b = 4 * lz + q;
+    return kLaneBuckets - 1 - (b < kLaneBuckets ? b : kLaneBuckets - 1);
+}
+
+// Positions [q0, q1) of a work-list item (false: nothing to run, or bad data,
+// which is flagged).
+__device__ __forceinline__ bool lane_item_range(const SliceArgs &g, uint32_t item, int64_t &q0,
+                                                int64_t &q1) {
+    const int64_t x = (int64_t)(item >> 1);
+    if (item & 1u) {  // a chain: row x
+        if (x >= g.a.dims[g.a.n]) return false;
+        const int64_t s = __ldg(g.row_ptr + x), e = __ldg(g.row_ptr + x + 1);
+        if (!slice_ok(g, s, e)) return false;
+        q0 = s;
+        q1 = e - s <= g.Lseq ? e : min(e, s + g.Lhead);
+        return q1 > q0;
+    }
+    if (x >= g.ntiles) return false;
+    if (!tile_inner(g, x, q0, q1)) {
+        atomicOr(g.a.err, kErrIndex);
+        return false;
+    }
+    return q1 > q0;
+}
+
+// The one-lane element-by-element walks of the pass -- tile interiors (runs of
+// whole slices) and chains (crossing slices, heads of long slices) -- from the
+// work list sorted by length: each warp takes the next 32 items, one per lane,
+// so the lanes of a warp walk about as many positions and the longest items
+// start first.  The factor row of each new slice is staged in the lane's ring
+// with the position that starts it; the finished row is written back when the
+// slice ends.
+template <int R, int J, typename VT>
+__global__ void __launch_bounds__(kLaneThreads) k_slices_lanes(SliceArgs g) {
+    constexpr int T = R / 4;
+    constexpr int P = SFT_LANE_P;
+    using LR = LaneRing<J, P, true>;
+    extern __shared__ __align__(16) float lane_ring[];
+    float *ring = lane_ring + threadIdx.x * LR::words;
+    const PassArgs &a = g.a;
+    const int lane = threadIdx.x & 31;
+    unsigned total = 0;
+    for (int b = lane; b < kLaneBuckets; b += 32) total += g.lane_cnt[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    unsigned *grab = g.lane_cnt + 2 * kLaneBuckets;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(grab, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        const unsigned k = base + (unsigned)lane;
+        int64_t q0 = 0, q1 = 0;
+        if (k >= total || !lane_item_range(g, g.lane_items[k], q0, q1)) continue;
         int32_t cur = -1;
         float av[J];
 #pragma unroll
         for (int q = 0; q < J; ++q) av[q] = 0.f;
-        walk_lane<J, kLaneTileP, true, VT>(g, ring, q0, q1,
-                                       [&](int32_t row, float x, bool ok, const float (&v)[J],
-                                           const float *newrow) {
+        walk_lane<J, P, true, VT>(g, ring, q0, q1,
+                                  [&](int32_t row, float x, bool ok, const float (&v)[J],
+                                      const float *newrow) {
             if (row != cur) {  // the slice changes: write the finished row, take the next
                 if (cur >= 0) store_run<J>(a.A + (int64_t)cur * J, av);
                 cur = row;
@@ -1629,6 +1677,9 @@ __global__ void __launch_bounds__(kCoreSliceThreads, SFT_CORE_MINB) k_slices_cor
     }
 }
 
+cudaError_t launch_lane_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
+                             int64_t *launches);
+
 template <typename K>
 inline int grid_for(K kernel, int threads, size_t smem, int64_t items_per_block, int64_t items,
                     int sms) {
@@ -1667,12 +1718,7 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
         *launches += 1;
     }
     if constexpr (FV && lane_kernels<R, J>()) {
-        constexpr size_t csm = (size_t)kLaneThreads * LaneRing<J, kLaneChainP, false>::words * 4;
-        constexpr size_t tsm = (size_t)kLaneThreads * LaneRing<J, kLaneTileP, true>::words * 4;
-        cudaFuncSetAttribute(k_slices_chains1<R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)csm);
-        cudaFuncSetAttribute(k_slices_tiles1<R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tsm);
+        static_assert(slice_lane_kernels(J), "host and device agree on the lane kernel");
         // blocked chains exist only if a chain may reach kGramMin positions
         const bool gram = g.gram && g.Lseq >= kGramMin;
         if (g.ntiles > 1) {
@@ -1689,14 +1735,19 @@ void factor_slices_t(const SliceArgs &g, bool with_maps, const SliceStreams &ss,
                     *launches += 1;
                 }
             }
-            const int gch = grid_for(k_slices_chains1<R, J, CT>, kLaneThreads, csm, kLaneThreads,
-                                     g.ntiles - 1, sms);
-            k_slices_chains1<R, J, CT><<<gch, kLaneThreads, csm, gram ? ss.tiles : ss.chains>>>(g);
-            *launches += 1;
         }
-        const int gd = grid_for(k_slices_tiles1<R, J, CT>, kLaneThreads, tsm, kLaneThreads, g.ntiles,
-                                sms);
-        k_slices_tiles1<R, J, CT><<<gd, kLaneThreads, tsm, ss.tiles>>>(g);
+        // tile interiors and the other chains: the sorted work list, then one
+        // persistent launch of the one-lane kernel
+        SliceArgs gl = g;
+        if (launch_lane_list(gl, (char *)g.maps + slice_lane_list_offset(g.ntiles, J), ss.tiles, sms,
+                             launches) != cudaSuccess)
+            return;
+        constexpr size_t lsm = (size_t)kLaneThreads * LaneRing<J, SFT_LANE_P, true>::words * 4;
+        cudaFuncSetAttribute(k_slices_lanes<R, J, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lsm);
+        const int gl_blocks = grid_for(k_slices_lanes<R, J, CT>, kLaneThreads, lsm, 1,
+                                       (int64_t)1 << 30, sms);
+        k_slices_lanes<R, J, CT><<<gl_blocks, kLaneThreads, lsm, ss.tiles>>>(gl);
         *launches += 1;
         return;
     }
@@ -1752,8 +1803,8 @@ SFT_SLICE_WRAPPERS(7, bf16)
 SFT_SLICE_WRAPPERS(15, bf16)
 #undef SFT_SLICE_WRAPPERS
 cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms);
-cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
-                              int64_t *launches);
+cudaError_t launch_chain_list(SliceArgs &g, void *list_ws, bool gram_only, cudaStream_t st,
+                              int sms, int64_t *launches);
 cudaError_t launch_piece_list(SliceArgs &g, void *list_ws, cudaStream_t st, int sms,
                               int64_t *launches);
 // fiber-shared v (k_slices_fv.cu): one instantiation per (R, J)
