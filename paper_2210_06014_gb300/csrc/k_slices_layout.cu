@@ -10,18 +10,26 @@
 // Factor pass (Eq. (9)-(10), element by element as in Algorithm 4).  During a
 // factor pass over mode n a nonzero reads and writes only a_{i_n}; slices are
 // independent, and running every slice's nonzeros one after another in visit
-// order reproduces the element-by-element rule exactly.  Work is cut into
-// tiles of W consecutive positions, one lane group (T = R/4 lanes) per tile:
-//   - a slice that lies inside a tile is run directly: the row stays in
-//     registers, each nonzero does e = x - a.(B p), a += lr (e v - lambda a);
-//   - a slice that crosses tile boundaries and has at most Lseq nonzeros is run
-//     directly, whole, by the group that owns its first boundary;
-//   - a longer slice is split at the tile boundaries.  One step is the affine
-//     map a -> M_t a + c_t with M_t = (1 - lr lambda) I - lr v v^T and
-//     c_t = lr x v, so each piece is composed into one map (M, c) in parallel
-//     (k_slices_maps) and k_slices_combine applies the pieces to the row in
-//     order.  This is the same recurrence, re-associated.
-// Nothing is atomic and the result is bitwise reproducible.
+// order reproduces the element-by-element rule exactly.  Positions are cut
+// into tiles of W; then
+//   - the slices inside a tile (its interior) are run directly: the row stays
+//     in registers, each nonzero does e = x - a.(B p), a += lr (e v - lambda a);
+//   - a slice that crosses tile boundaries and has at most Lseq nonzeros is
+//     run directly, whole, as one chain;
+//   - a longer slice runs its first Lhead = Lseq nonzeros as a chain (its head)
+//     and the rest (its map region) split at the tile boundaries.  One step is
+//     the affine map a -> M_t a + c_t with M_t = (1 - lr lambda) I - lr v v^T
+//     and c_t = lr x v, so each piece is composed into one map (M, c) in
+//     parallel (k_slices_maps); k_slices_compose multiplies blocks of
+//     consecutive piece maps and k_slices_combine applies them to the row, in
+//     order, after its head.  This is the same recurrence, re-associated.
+// With the fiber table and J_n <= 16 the interiors and the chains are one
+// work list sorted by length (k_lane_count / k_lane_scatter) that a
+// persistent kernel walks one item per lane (k_slices_lanes); chains of
+// 4096+ positions go to the blocked kernel (k_slices_gram).  Otherwise lane
+// groups of R/4 lanes walk them (k_slices_tiles / k_slices_chains).  The
+// atomics only build the lists, whose order affects no result: the pass is
+// bitwise reproducible.
 //
 // Core pass (Eq. (9), (11), Algorithm 5).  With A^(n) fixed,
 //   G = sum_s e_s a_{i_n(s)} p_s^T = sum_slices a_i (sum_{s in slice} e_s p_s)^T,
