@@ -1,6 +1,6 @@
 /*
  * sft_batch.h -- many independent sparse FastTucker decompositions trained
- * together by one persistent kernel per epoch (GB300, sm_103a).
+ * together by one graph launch per epoch (GB300, sm_103a).
  *
  * The paper trains one tensor at a time.  This interface runs the same epoch
  * of Algorithm 2 on a set of unrelated problems at once: every problem's
@@ -12,11 +12,13 @@
  * How it runs: the library cuts every pass into tasks (`chunk` nonzeros, or
  * 4096 rows of C) and orders all tasks of all problems with a list scheduler
  * (problems with the most remaining work first).  That order respects each
- * problem's chain of passes.  One persistent kernel hands the tasks out in
- * that order.  A task whose predecessor pass is still running waits on a
- * device counter with a bounded poll.  The reset of the counters plus the
- * persistent kernel are captured once as a CUDA graph and replayed every
- * epoch.  sft_batch_autotune picks `chunk` and the CTAs per SM by timing
+ * problem's chain of passes.  The problems are split by rank into two
+ * classes (R <= 16 and R = 32), each with its own list and its own
+ * persistent kernel compiled for those ranks only; the two kernels run side
+ * by side and hand their tasks out in list order.  A task whose predecessor
+ * pass is still running waits on a device counter with a bounded poll.  The
+ * reset of the counters plus the persistent kernels are captured once as a
+ * CUDA graph and replayed every epoch.  sft_batch_autotune picks `chunk` and the CTAs per SM by timing
  * epochs.
  *
  * Update rules (as the single-problem calls with deterministic = 0):
@@ -35,7 +37,8 @@
  * `prec`, idx[n] int32 and val float32 with nnz entries, all row-major,
  * 16-byte aligned).  The caller also provides the workspace (device, 256-byte
  * aligned) sized by sft_batch_workspace_bytes.  The handle owns host metadata,
- * one private stream used for graph capture, and the instantiated graphs.
+ * two private streams and two events used for graph capture, and the
+ * instantiated graphs.
  *
  * Errors: argument errors return before any launch.  Bad coordinates are
  * skipped by the kernel and reported by sft_batch_sync / sft_batch_loss as
@@ -119,7 +122,8 @@ sft_status sft_batch_set_wait_limit(sft_batch *b, int64_t polls);
  * kernel stops, SFT_ETIMEOUT); hold = 0 undoes it.  Nothing faults. */
 sft_status sft_batch_hold_pass(sft_batch *b, int32_t prob, int32_t hold);
 
-/* Persistent-kernel launches enqueued so far (one per refresh, epoch, loss). */
+/* Graph launches enqueued so far (one per refresh, epoch, loss; each runs
+ * the persistent kernel of every rank class that has tasks). */
 int64_t sft_batch_launch_count(const sft_batch *b);
 
 /* Tasks in one epoch's list with the current chunk. */
@@ -135,8 +139,10 @@ typedef struct {
 } sft_batch_task_info;
 
 /* Host only (no GPU needed): the task list sft_batch_create builds for
- * plan 0 (epoch), 1 (refresh) or 2 (loss) with tasks of `chunk` nonzeros
- * ordered for `workers` CTAs.  Writes at most cap records to out (host) and
+ * plan 0 (epoch), 1 (refresh) or 2 (loss) with tasks of `chunk` nonzeros:
+ * the tasks of the problems with R <= 16, then those of the problems with
+ * R = 32 (each part run by its own persistent kernel), each part ordered
+ * for `workers` CTAs.  Writes at most cap records to out (host) and
  * returns the full task count, or -1 on invalid arguments. */
 int64_t sft_batch_plan(int32_t nprob, const sft_batch_problem *probs, int32_t plan, int64_t chunk,
                        int32_t workers, sft_batch_task_info *out, int64_t cap);

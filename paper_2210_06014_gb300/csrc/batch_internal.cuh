@@ -66,7 +66,23 @@ struct BatchArgs {
 
 // kErrWait (sft_internal.cuh): a dependency wait ran out of polls
 
-cudaError_t launch_batch(const BatchArgs &g, bool cbf16, int grid, cudaStream_t st);
-int batch_blocks_per_sm(bool cbf16);
+// Problems are split by R into classes, each run by its own persistent
+// kernel compiled for those R only, so that the kernel of the small ranks
+// is not held at the register count of R = 32: class 0 holds R <= 16,
+// class 1 R = 32.  The two kernels share the plan's counters (problems of
+// different classes never wait on each other) and run side by side.
+constexpr int kBatchClasses = 2;
+inline int batch_class(int R) { return R <= 16 ? 0 : 1; }
+
+struct BatchLaunch {
+    BatchArgs cls[kBatchClasses];  // tasks, count and head of each class (same counters)
+    int grid[kBatchClasses];       // persistent CTAs of each class's kernel
+};
+
+// Counter reset, then the class kernels that have tasks (class 1 on `side`,
+// forked from and joined back to `st` with the two events).
+cudaError_t launch_batch(const BatchLaunch &L, bool cbf16, cudaStream_t st, cudaStream_t side,
+                         cudaEvent_t fork, cudaEvent_t join);
+int batch_blocks_per_sm(bool cbf16, int cls);
 
 }  // namespace sft

@@ -30,6 +30,23 @@
 //            the slots in order
 #include "batch_internal.cuh"
 
+// One-ahead gathers of the task loops (1) or gathers at use (0), and the
+// minimum resident CTAs per SM asked of the register allocator for the
+// kernels of the small ranks (class 0) and of R = 32 (class 1).  Measured on
+// the 64-problem workload (epoch ms, class 1 at 1 CTA per SM): gathers at use
+// with 3 CTAs per SM for class 0 44.0; 2 CTAs 45.9; 4 CTAs 45.6; one-ahead
+// gathers 46.2 (2 CTAs) and 64.1 (3 CTAs, spilling); then class 1 at 2 CTAs
+// per SM (128 registers) 38.6.
+#ifndef SFT_BATCH_PREFETCH
+#define SFT_BATCH_PREFETCH 0
+#endif
+#ifndef SFT_BATCH_MINB0
+#define SFT_BATCH_MINB0 3
+#endif
+#ifndef SFT_BATCH_MINB1
+#define SFT_BATCH_MINB1 2
+#endif
+
 namespace sft {
 
 namespace {
@@ -91,20 +108,71 @@ struct NextSample {
     }
 };
 
-// Lane's 4 entries of prod_{k != skip} C^(k)[i_k] (skip = -1: every mode).
-template <int R, typename CT>
-__device__ __forceinline__ float4 gather_product(const BatchProblem &P,
-                                                 const int32_t (&ik)[kBatchMaxOrder], bool ok,
-                                                 int skip, int sub) {
-    float4 p = make_float4(1.f, 1.f, 1.f, 1.f);
+// One nonzero of a lane group with its gathered rows: the lane's 4 entries of
+// C^(k)[i_k] for k != skip (skip = -1: every mode) and, where the task needs
+// it, of the factor row a_{i_n}.  Loaded one iteration before use, so a lane
+// group has two nonzeros' gathers in flight.
+struct Gathered {
     float4 c[kBatchMaxOrder];
+    float4 a;
+    int32_t in;
+    float x;
+    bool ok;
+};
+
+template <int R, typename CT, bool WITH_A>
+__device__ __forceinline__ void gather(const BatchProblem &P, const NextSample &nxt, bool valid,
+                                       int skip, int sub, Gathered &g, int *err) {
+    int32_t ik[kBatchMaxOrder];
+    g.ok = nxt.take(P, valid, skip, ik, g.in, g.x, err);
 #pragma unroll
     for (int k = 0; k < kBatchMaxOrder; ++k)
-        c[k] = (ok && k < P.N && k != skip) ? ldCcg<CT>(P.C[k], (int64_t)ik[k] * R + 4 * sub)
-                                            : make_float4(1.f, 1.f, 1.f, 1.f);
+        g.c[k] = (g.ok && k < P.N && k != skip) ? ldCcg<CT>(P.C[k], (int64_t)ik[k] * R + 4 * sub)
+                                                : make_float4(1.f, 1.f, 1.f, 1.f);
+    if constexpr (WITH_A)
+        g.a = g.ok ? __ldcg(reinterpret_cast<const float4 *>(P.A[skip] + (int64_t)g.in * R) + sub)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Lane's 4 entries of the product of the gathered rows.
+__device__ __forceinline__ float4 product(const Gathered &g) {
+    float4 p = make_float4(1.f, 1.f, 1.f, 1.f);
 #pragma unroll
-    for (int k = 0; k < kBatchMaxOrder; ++k) mul4(p, c[k]);
+    for (int k = 0; k < kBatchMaxOrder; ++k) mul4(p, g.c[k]);
     return p;
+}
+
+// The lane group's nonzeros of a task, s = begin + warp GPW + gw, then every
+// kWarps GPW: body(g) for each with its gathered rows (g.ok false past the
+// end).  The loop bound is uniform over the warp.
+template <int R, typename CT, bool WITH_A, typename Body>
+__device__ __forceinline__ void walk_chunk(const BatchProblem &P, const BatchTask &tk, int skip,
+                                           int sub, int gw, int warp, int *err, Body &&body) {
+    constexpr int T = R / 4, GPW = 32 / T;
+    constexpr int64_t STEP = (int64_t)kWarps * GPW;
+    const int64_t s0 = tk.begin + (int64_t)warp * GPW + gw;
+    NextSample nxt;
+    nxt.fetch(P, s0, tk.end);
+    Gathered cur;
+    if constexpr (SFT_BATCH_PREFETCH) {
+        gather<R, CT, WITH_A>(P, nxt, s0 < tk.end, skip, sub, cur, err);
+        nxt.fetch(P, s0 + STEP, tk.end);
+    }
+    for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += STEP) {
+        const int64_t s = t0 + gw;
+        if constexpr (SFT_BATCH_PREFETCH) {
+            // the next nonzero's gathers go out before this one is formed
+            Gathered nx;
+            gather<R, CT, WITH_A>(P, nxt, s + STEP < tk.end, skip, sub, nx, err);
+            nxt.fetch(P, s + 2 * STEP, tk.end);
+            body(cur);
+            cur = nx;
+        } else {
+            gather<R, CT, WITH_A>(P, nxt, s < tk.end, skip, sub, cur, err);
+            nxt.fetch(P, s + STEP, tk.end);
+            body(cur);
+        }
+    }
 }
 
 // B^(n) (R x R) into shared memory.
@@ -134,35 +202,26 @@ __device__ __forceinline__ float residual(const float *sB, const float4 &p, cons
 
 template <int R, typename CT>
 __device__ void task_factor(const BatchProblem &P, const BatchTask &tk, float *sB, int *err) {
-    constexpr int T = R / 4, GPW = 32 / T;
+    constexpr int T = R / 4;
     stage_B<R>(P.B[tk.mode], sB);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (T - 1), gw = lane / T;
     const int n = tk.mode;
     float *An = P.A[n];
-    NextSample nxt;
-    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
-    for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
-        const int64_t s = t0 + gw;
-        int32_t ik[kBatchMaxOrder], in;
-        float x;
-        const bool ok = nxt.take(P, s < tk.end, n, ik, in, x, err);
-        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
-        const float4 p = gather_product<R, CT>(P, ik, ok, n, sub);
-        float *arow = An + (int64_t)in * R + 4 * sub;
-        const float4 a = ok ? __ldcg(reinterpret_cast<const float4 *>(arow))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    walk_chunk<R, CT, true>(P, tk, n, sub, gw, warp, err, [&](const Gathered &cur) {
+        const float4 p = product(cur);
+        const float4 a = cur.a;
         float v[R];
-        const float e = residual<R>(sB, p, a, x, ok, sub, v);
-        if (ok) {
+        const float e = residual<R>(sB, p, a, cur.x, cur.ok, sub, v);
+        if (cur.ok) {
             float4 d;
             d.x = P.lrA * (e * v[0] - P.lamA * a.x);
             d.y = P.lrA * (e * v[1] - P.lamA * a.y);
             d.z = P.lrA * (e * v[2] - P.lamA * a.z);
             d.w = P.lrA * (e * v[3] - P.lamA * a.w);
-            atomicAdd(reinterpret_cast<float4 *>(arow), d);
+            atomicAdd(reinterpret_cast<float4 *>(An + (int64_t)cur.in * R + 4 * sub), d);
         }
-    }
+    });
 }
 
 template <int R, typename CT>
@@ -211,19 +270,12 @@ __device__ void task_core(const BatchProblem &P, const BatchTask &tk, float *sB,
 #pragma unroll
     for (int q = 0; q < EPL; ++q) acc[q] = tot[q] = 0.f;
     int fold = 0;
-    NextSample nxt;
-    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
-    for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
-        const int64_t s = t0 + gw;
-        int32_t ik[kBatchMaxOrder], in;
-        float x;
-        const bool ok = nxt.take(P, s < tk.end, n, ik, in, x, err);
-        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
-        const float4 p = gather_product<R, CT>(P, ik, ok, n, sub);
-        const float4 a = ok ? __ldcg(reinterpret_cast<const float4 *>(P.A[n] + (int64_t)in * R) + sub)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    walk_chunk<R, CT, true>(P, tk, n, sub, gw, warp, err, [&](const Gathered &cur) {
+        const bool ok = cur.ok;
+        const float4 p = product(cur);
+        const float4 a = cur.a;
         float v[R];
-        const float e = residual<R>(sB, p, a, x, ok, sub, v);
+        const float e = residual<R>(sB, p, a, cur.x, ok, sub, v);
         *reinterpret_cast<float4 *>(&sea[gw * R + 4 * sub]) =
             make_float4(e * a.x, e * a.y, e * a.z, e * a.w);
         *reinterpret_cast<float4 *>(&spp[gw * R + 4 * sub]) =
@@ -246,7 +298,7 @@ __device__ void task_core(const BatchProblem &P, const BatchTask &tk, float *sB,
                 acc[q] = 0.f;
             }
         }
-    }
+    });
     __syncthreads();  // staging becomes the reduction area
     if (active) {
 #pragma unroll
@@ -277,26 +329,19 @@ __device__ void task_apply(const BatchProblem &P, const BatchTask &tk) {
 
 template <int R, typename CT>
 __device__ void task_loss(const BatchProblem &P, const BatchTask &tk, double *sred, int *err) {
-    constexpr int T = R / 4, GPW = 32 / T;
+    constexpr int T = R / 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (T - 1), gw = lane / T;
     double s2 = 0.0, s1 = 0.0;
-    NextSample nxt;
-    nxt.fetch(P, tk.begin + (int64_t)warp * GPW + gw, tk.end);
-    for (int64_t t0 = tk.begin + (int64_t)warp * GPW; t0 < tk.end; t0 += (int64_t)kWarps * GPW) {
-        const int64_t s = t0 + gw;
-        int32_t ik[kBatchMaxOrder], in;
-        float x;
-        const bool ok = nxt.take(P, s < tk.end, -1, ik, in, x, err);
-        nxt.fetch(P, s + (int64_t)kWarps * GPW, tk.end);
-        const float4 p = gather_product<R, CT>(P, ik, ok, -1, sub);
+    walk_chunk<R, CT, false>(P, tk, -1, sub, gw, warp, err, [&](const Gathered &cur) {
+        const float4 p = product(cur);
         const float xh = group_sum<T>((p.x + p.y) + (p.z + p.w));
-        if (ok && sub == 0) {
-            const double e = (double)x - (double)xh;
+        if (cur.ok && sub == 0) {
+            const double e = (double)cur.x - (double)xh;
             s2 += e * e;
             s1 += fabs(e);
         }
-    }
+    });
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) {
         s2 += __shfl_xor_sync(kFull, s2, w);
@@ -344,10 +389,12 @@ __device__ void run_task(const BatchProblem &P, const BatchTask &tk, float *sB, 
     }
 }
 
-template <typename CT>
-__global__ void __launch_bounds__(kBatchThreads) k_batch_run(BatchArgs g) {
+template <typename CT, int CLS>
+__global__ void __launch_bounds__(kBatchThreads, CLS == 0 ? SFT_BATCH_MINB0 : SFT_BATCH_MINB1)
+    k_batch_run(BatchArgs g) {
     __shared__ __align__(16) float sB[32 * 32];
     __shared__ __align__(16) float sbuf[kWarps * 32 * 32];
+    __shared__ __align__(16) BatchProblem sP;  // the task's problem record
     __shared__ int s_task;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -379,13 +426,23 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_run(BatchArgs g) {
         const int t = s_task;
         if (t < 0) break;
         const BatchTask tk = g.tasks[t];
-        const BatchProblem &P = g.probs[tk.prob];
-        switch (P.R) {
-            case 4: run_task<4, CT>(P, tk, sB, sbuf, g.err); break;
-            case 8: run_task<8, CT>(P, tk, sB, sbuf, g.err); break;
-            case 16: run_task<16, CT>(P, tk, sB, sbuf, g.err); break;
-            case 32: run_task<32, CT>(P, tk, sB, sbuf, g.err); break;
-            default: break;
+        // the problem record (pointers, sizes, rates) into shared memory, so
+        // that the task loops read it there instead of holding it in registers
+        static_assert(sizeof(BatchProblem) % 4 == 0, "record copied as words");
+        for (int q = threadIdx.x; q < (int)(sizeof(BatchProblem) / 4); q += blockDim.x)
+            reinterpret_cast<int32_t *>(&sP)[q] =
+                reinterpret_cast<const int32_t *>(g.probs + tk.prob)[q];
+        __syncthreads();
+        const BatchProblem &P = sP;
+        if constexpr (CLS == 0) {
+            switch (P.R) {
+                case 4: run_task<4, CT>(P, tk, sB, sbuf, g.err); break;
+                case 8: run_task<8, CT>(P, tk, sB, sbuf, g.err); break;
+                case 16: run_task<16, CT>(P, tk, sB, sbuf, g.err); break;
+                default: break;
+            }
+        } else {
+            if (P.R == 32) run_task<32, CT>(P, tk, sB, sbuf, g.err);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -395,24 +452,24 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_run(BatchArgs g) {
     }
 }
 
-// Counters back to their starting values and the task cursor to 0.
-__global__ void k_batch_reset(BatchArgs g) {
+// Counters back to their starting values and the classes' task cursors to 0.
+__global__ void k_batch_reset(BatchArgs g, int32_t *head1) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.ncounters; i += gridDim.x * blockDim.x)
         g.counters[i] = g.init[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *g.head = 0;
+        *head1 = 0;
         *g.abort = 0;
     }
 }
 
-}  // namespace
-
-int batch_blocks_per_sm(bool cbf16) {
+template <typename CT>
+int blocks_per_sm(int cls) {
     int n = 0;
-    cudaError_t e = cbf16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &n, k_batch_run<__nv_bfloat16>, kBatchThreads, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &n, k_batch_run<float>, kBatchThreads, 0);
+    cudaError_t e = cls == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &n, k_batch_run<CT, 0>, kBatchThreads, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &n, k_batch_run<CT, 1>, kBatchThreads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -420,16 +477,43 @@ int batch_blocks_per_sm(bool cbf16) {
     return n < 1 ? 1 : n;
 }
 
-cudaError_t launch_batch(const BatchArgs &g, bool cbf16, int grid, cudaStream_t st) {
-    const int rblocks = g.ncounters > 0 ? (g.ncounters + 255) / 256 : 1;
-    k_batch_reset<<<rblocks, 256, 0, st>>>(g);
+template <typename CT>
+void launch_class(const BatchArgs &g, int cls, int grid, cudaStream_t st) {
+    if (cls == 0) k_batch_run<CT, 0><<<grid, kBatchThreads, 0, st>>>(g);
+    else k_batch_run<CT, 1><<<grid, kBatchThreads, 0, st>>>(g);
+}
+
+}  // namespace
+
+int batch_blocks_per_sm(bool cbf16, int cls) {
+    return cbf16 ? blocks_per_sm<__nv_bfloat16>(cls) : blocks_per_sm<float>(cls);
+}
+
+cudaError_t launch_batch(const BatchLaunch &L, bool cbf16, cudaStream_t st, cudaStream_t side,
+                         cudaEvent_t fork, cudaEvent_t join) {
+    const BatchArgs &g0 = L.cls[0];
+    const int rblocks = g0.ncounters > 0 ? (g0.ncounters + 255) / 256 : 1;
+    k_batch_reset<<<rblocks, 256, 0, st>>>(g0, L.cls[1].head);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (g.ntasks == 0) return cudaSuccess;
-    if (cbf16)
-        k_batch_run<__nv_bfloat16><<<grid, kBatchThreads, 0, st>>>(g);
-    else
-        k_batch_run<float><<<grid, kBatchThreads, 0, st>>>(g);
+    const bool has0 = L.cls[0].ntasks > 0, has1 = L.cls[1].ntasks > 0;
+    auto run = [&](int cls, cudaStream_t s) {
+        if (cbf16) launch_class<__nv_bfloat16>(L.cls[cls], cls, L.grid[cls], s);
+        else launch_class<float>(L.cls[cls], cls, L.grid[cls], s);
+    };
+    if (has0 && has1) {
+        // the R = 32 kernel (the longer tasks) on the side stream, first
+        if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+        run(1, side);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+        run(0, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return cudaStreamWaitEvent(st, join, 0);
+    }
+    if (has0) run(0, st);
+    else if (has1) run(1, st);
     return cudaGetLastError();
 }
 

@@ -85,7 +85,7 @@ Layout make_layout(const std::vector<HostProblem> &ps, int64_t min_chunk) {
     L.abort = off;
     off = align_up(off + sizeof(int32_t));
     L.head = off;
-    off = align_up(off + kPlans * sizeof(int32_t));
+    off = align_up(off + kPlans * kBatchClasses * sizeof(int32_t));
     for (int pl = 0; pl < kPlans; ++pl) {
         PlanSize s = plan_size(ps, pl, min_chunk);
         L.cap_tasks[pl] = s.tasks;
@@ -236,7 +236,11 @@ std::vector<std::vector<Phase>> make_phases(const std::vector<HostProblem> &ps, 
 // in its chain.  The dispatch order is a topological order of the task graph
 // (a task is emitted only after every task of the phase it waits for has
 // been emitted), which is what the persistent kernel's waits rely on.
-std::vector<BatchTask> order_tasks(std::vector<std::vector<Phase>> &chains, int workers,
+// Only the chains of problems with use[p] set are scheduled; `init` (sized by
+// the caller to every counter of the plan) receives their counters' starting
+// values.
+std::vector<BatchTask> order_tasks(std::vector<std::vector<Phase>> &chains,
+                                   const std::vector<char> &use, int workers,
                                    std::vector<int32_t> *init) {
     struct Ready {
         double rest;
@@ -251,16 +255,14 @@ std::vector<BatchTask> order_tasks(std::vector<std::vector<Phase>> &chains, int 
     std::priority_queue<Ready> ready;
     std::priority_queue<Event, std::vector<Event>, std::greater<Event>> events;
     std::vector<std::vector<int>> dispatched(chains.size()), finished(chains.size());
-    int ncounters = 0;
     for (size_t p = 0; p < chains.size(); ++p) {
         dispatched[p].assign(chains[p].size(), 0);
         finished[p].assign(chains[p].size(), 0);
-        ncounters += (int)chains[p].size();
     }
-    init->assign(ncounters, 0);
     // a chain's first phase with tasks is ready at once (phases without
     // tasks cannot occur: every problem has nnz >= 1 and I_n >= 1)
     for (size_t p = 0; p < chains.size(); ++p) {
+        if (!use[p]) continue;
         for (const Phase &ph : chains[p]) (*init)[ph.counter] = ph.ntasks;
         for (size_t k = 0; k < chains[p].size(); ++k) {
             const bool head = chains[p][k].wait < 0;
@@ -305,14 +307,42 @@ std::vector<BatchTask> order_tasks(std::vector<std::vector<Phase>> &chains, int 
     return out;
 }
 
+int count_counters(const std::vector<std::vector<Phase>> &chains) {
+    int n = 0;
+    for (const auto &c : chains) n += (int)c.size();
+    return n;
+}
+
+// The plan's task list: the list of class 0 (R <= 16) followed by that of
+// class 1 (R = 32), each scheduled on its own kernel's CTAs; n[c] = tasks of
+// class c.
+std::vector<BatchTask> class_lists(const std::vector<HostProblem> &ps,
+                                   std::vector<std::vector<Phase>> &chains,
+                                   const int (&workers)[kBatchClasses], std::vector<int32_t> *init,
+                                   int64_t (&n)[kBatchClasses]) {
+    init->assign(count_counters(chains), 0);
+    std::vector<BatchTask> out;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        std::vector<char> use(ps.size(), 0);
+        for (size_t p = 0; p < ps.size(); ++p) use[p] = batch_class(ps[p].R) == c;
+        std::vector<BatchTask> t = order_tasks(chains, use, workers[c], init);
+        n[c] = (int64_t)t.size();
+        out.insert(out.end(), t.begin(), t.end());
+    }
+    return out;
+}
+
 }  // namespace
 
 struct sft_batch {
     std::vector<HostProblem> ps;
     int cbf16 = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;  // private stream for graph capture
-    int device = 0, sms = 1, max_bps = 1;
+    cudaStream_t cap = nullptr;   // private stream for graph capture
+    cudaStream_t side = nullptr;  // ... and its fork for the second class kernel
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int device = 0, sms = 1;
+    int max_bps[kBatchClasses] = {1, 1};
     char *ws = nullptr;
     Layout L;
     int64_t min_chunk = kMinChunk, chunk = kMinChunk;
@@ -320,7 +350,7 @@ struct sft_batch {
     int64_t wait_limit = kWaitLimit;
     std::vector<int32_t> epoch_init;   // starting counters of the epoch list (host copy)
     std::vector<int32_t> epoch_first;  // per problem: counter of its first epoch pass
-    BatchArgs args[kPlans] = {};
+    BatchLaunch args[kPlans] = {};
     cudaGraphExec_t exec[kPlans] = {nullptr, nullptr, nullptr};
     int64_t launches = 0;
     std::string last_error;
@@ -344,8 +374,19 @@ void drop_graphs(sft_batch *b) {
     }
 }
 
+// Graphs, streams, events and the handle itself.
+void release(sft_batch *b) {
+    drop_graphs(b);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
 // Builds the three task lists for (chunk, bps), uploads them and captures
-// one graph per list (counter reset + persistent kernel).
+// one graph per list (counter reset + the persistent kernel of each class;
+// bps is capped by each class kernel's occupancy).
 sft_status build_plans(sft_batch *b, int64_t chunk, int bps) {
     // the old lists and graphs may still be in use by enqueued work
     cudaError_t se = cudaStreamSynchronize(b->stream);
@@ -353,11 +394,13 @@ sft_status build_plans(sft_batch *b, int64_t chunk, int bps) {
     drop_graphs(b);
     b->chunk = chunk;
     b->bps = bps;
-    const int grid = b->sms * bps;
+    int grid[kBatchClasses];
+    for (int c = 0; c < kBatchClasses; ++c) grid[c] = b->sms * std::min(bps, b->max_bps[c]);
     for (int pl = 0; pl < kPlans; ++pl) {
         auto chains = make_phases(b->ps, pl, chunk);
         std::vector<int32_t> init;
-        std::vector<BatchTask> tasks = order_tasks(chains, grid, &init);
+        int64_t ncls[kBatchClasses];
+        std::vector<BatchTask> tasks = class_lists(b->ps, chains, grid, &init, ncls);
         if ((int64_t)tasks.size() > b->L.cap_tasks[pl] || (int64_t)init.size() > b->L.cap_counters[pl])
             return fail(b, SFT_ENOMEM, "task list larger than the workspace allows");
         BatchTask *dt = (BatchTask *)(b->ws + b->L.tasks[pl]);
@@ -368,17 +411,23 @@ sft_status build_plans(sft_batch *b, int64_t chunk, int bps) {
         if (e == cudaSuccess)
             e = cudaMemcpy(di, init.data(), init.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(b, e, "task list upload");
-        BatchArgs &g = b->args[pl];
-        g.probs = (const BatchProblem *)(b->ws + b->L.probs);
-        g.tasks = dt;
-        g.ntasks = (int32_t)tasks.size();
-        g.counters = dc;
-        g.init = di;
-        g.ncounters = (int32_t)init.size();
-        g.head = (int32_t *)(b->ws + b->L.head) + pl;
-        g.abort = (int32_t *)(b->ws + b->L.abort);
-        g.err = (int *)(b->ws + b->L.err);
-        g.wait_limit = b->wait_limit;
+        BatchLaunch &bl = b->args[pl];
+        int64_t base = 0;
+        for (int c = 0; c < kBatchClasses; ++c) {
+            BatchArgs &g = bl.cls[c];
+            g.probs = (const BatchProblem *)(b->ws + b->L.probs);
+            g.tasks = dt + base;
+            g.ntasks = (int32_t)ncls[c];
+            g.counters = dc;
+            g.init = di;
+            g.ncounters = (int32_t)init.size();
+            g.head = (int32_t *)(b->ws + b->L.head) + pl * kBatchClasses + c;
+            g.abort = (int32_t *)(b->ws + b->L.abort);
+            g.err = (int *)(b->ws + b->L.err);
+            g.wait_limit = b->wait_limit;
+            bl.grid[c] = grid[c];
+            base += ncls[c];
+        }
         if (pl == kPlanEpoch) {
             b->epoch_init = init;
             b->epoch_first.assign(b->ps.size(), -1);
@@ -388,7 +437,7 @@ sft_status build_plans(sft_batch *b, int64_t chunk, int bps) {
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(b, e, "graph capture");
-        cudaError_t le = launch_batch(g, b->cbf16 != 0, grid, b->cap);
+        cudaError_t le = launch_batch(bl, b->cbf16 != 0, b->cap, b->side, b->fork, b->join);
         e = cudaStreamEndCapture(b->cap, &graph);
         if (le != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -472,13 +521,17 @@ sft_status sft_batch_create(int32_t nprob, const sft_batch_problem *probs, int32
     b->min_chunk = min_chunk;
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        delete b;
+        release(b);
         return SFT_ECUDA;
     }
-    b->max_bps = batch_blocks_per_sm(b->cbf16 != 0);
-    int bps = blocks_per_sm == 0 ? b->max_bps : std::min<int>(blocks_per_sm, b->max_bps);
+    for (int c = 0; c < kBatchClasses; ++c) b->max_bps[c] = batch_blocks_per_sm(b->cbf16 != 0, c);
+    const int maxb = std::max(b->max_bps[0], b->max_bps[1]);
+    int bps = blocks_per_sm == 0 ? maxb : std::min<int>(blocks_per_sm, maxb);
     // problem table
     std::vector<BatchProblem> table(b->ps.size());
     for (size_t i = 0; i < b->ps.size(); ++i) {
@@ -508,15 +561,12 @@ sft_status sft_batch_create(int32_t nprob, const sft_batch_problem *probs, int32
                                cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->ws + L.err, 0, sizeof(int));
     if (e != cudaSuccess) {
-        cudaStreamDestroy(b->cap);
-        delete b;
+        release(b);
         return SFT_ECUDA;
     }
     st = build_plans(b, chunk, bps);
     if (st != SFT_OK) {
-        drop_graphs(b);
-        cudaStreamDestroy(b->cap);
-        delete b;
+        release(b);
         return st;
     }
     *out = b;
@@ -595,8 +645,9 @@ sft_status sft_batch_autotune(sft_batch *b, void *scratch, size_t scratch_bytes,
         chunks.push_back(c);
     }
     std::vector<int> bpss;
-    for (int v : {1, 2, b->max_bps})
-        if (v <= b->max_bps && std::find(bpss.begin(), bpss.end(), v) == bpss.end()) bpss.push_back(v);
+    const int maxb = std::max(b->max_bps[0], b->max_bps[1]);
+    for (int v : {1, 2, maxb})
+        if (v <= maxb && std::find(bpss.begin(), bpss.end(), v) == bpss.end()) bpss.push_back(v);
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess) return cuda_fail(b, cudaGetLastError(), "event");
     if (cudaEventCreate(&t1) != cudaSuccess) {
@@ -665,7 +716,9 @@ int64_t sft_batch_plan(int32_t nprob, const sft_batch_problem *probs, int32_t pl
     if (plan < 0 || plan >= kPlans || chunk < kMinChunk || workers < 1 || cap < 0) return -1;
     auto chains = make_phases(ps, plan, chunk);
     std::vector<int32_t> init;
-    std::vector<BatchTask> tasks = order_tasks(chains, workers, &init);
+    int64_t ncls[kBatchClasses];
+    const int w[kBatchClasses] = {workers, workers};
+    std::vector<BatchTask> tasks = class_lists(ps, chains, w, &init, ncls);
     const int64_t n = (int64_t)tasks.size();
     if (out && cap > 0) std::memcpy(out, tasks.data(), (size_t)std::min(n, cap) * sizeof(BatchTask));
     return n;
@@ -694,15 +747,18 @@ sft_status sft_batch_hold_pass(sft_batch *b, int32_t prob, int32_t hold) {
 
 int64_t sft_batch_launch_count(const sft_batch *b) { return b ? b->launches : 0; }
 
-int64_t sft_batch_epoch_tasks(const sft_batch *b) { return b ? b->args[kPlanEpoch].ntasks : 0; }
+int64_t sft_batch_epoch_tasks(const sft_batch *b) {
+    if (!b) return 0;
+    int64_t n = 0;
+    for (int c = 0; c < kBatchClasses; ++c) n += b->args[kPlanEpoch].cls[c].ntasks;
+    return n;
+}
 
 const char *sft_batch_last_error(const sft_batch *b) { return b ? b->last_error.c_str() : "null handle"; }
 
 void sft_batch_destroy(sft_batch *b) {
     if (!b) return;
-    drop_graphs(b);
-    if (b->cap) cudaStreamDestroy(b->cap);
-    delete b;
+    release(b);
 }
 
 }  // extern "C"

@@ -87,9 +87,15 @@ def test_refresh_and_loss_plans(sft):
 
 
 def test_big_problems_start_first(sft):
-    """The list scheduler hands out the problem with the most work first."""
+    """The list is the problems with R <= 16, then those with R = 32 (one
+    persistent kernel each); within each part the list scheduler hands out
+    the problem with the most work first."""
     tasks = plan(sft, 0, 256, 4)
-    assert tasks[0]["prob"] == 2  # 70k nonzeros at R = 32
+    small = [p for p, (_, R, _) in enumerate(SHAPES) if R <= 16]
+    cls = [0 if t["prob"] in small else 1 for t in tasks]
+    assert cls == sorted(cls)  # the R <= 16 part, then the R = 32 part
+    assert tasks[0]["prob"] == 0  # 20k nonzeros at R = 8: most work of the small ranks
+    assert tasks[cls.index(1)]["prob"] == 2  # the only R = 32 problem
 
 
 @pytest.mark.parametrize("shape", [((10, 10), 12, 100), ((10,) * 9, 8, 100), ((10, 10), 8, 0)])
