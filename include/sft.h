@@ -196,8 +196,8 @@ sft_status sft_grad_AB(sft_ctx *ctx, const float *const *dC, const double *scale
 /* Bytes of device scratch sft_group_slices needs for nnz nonzeros. */
 size_t sft_slices_scratch_bytes(int64_t nnz);
 
-/* Build the slice layout of mode `mode` on the device (a bitonic sort of
- * (i_mode, position) keys, then a gather).  out_idx: N device arrays of nnz
+/* Build the slice layout of mode `mode` on the device (a stable radix sort of
+ * (i_mode, position) keys by i_mode, then a gather).  out_idx: N device arrays of nnz
  * int32; out_val: nnz float32; out_row_ptr: I_mode + 1 int32.  perm as in
  * sft_update_factors (NULL = storage order).  Nonzeros with a coordinate out
  * of range are moved behind the last slice and flagged (SFT_EINVAL at the next

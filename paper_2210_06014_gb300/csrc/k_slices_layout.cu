@@ -2,10 +2,11 @@
 // mode-n slices of the tensor (all nonzeros that share i_n, kept in visit
 // order), the CSF layout of Section "Tensor Storage Format".
 //
-// Layout.  k_slice_keys / k_bitonic_* / k_slice_gather / k_slice_rowptr sort
-// the visit positions by (i_n, position) -- a bitonic sort of unique 64-bit
-// keys, so the order inside a slice is the visit order -- and copy the COO
-// arrays into that order; row_ptr[i] is the first position of slice i.
+// Layout.  k_slice_keys / k_rs_* (a stable radix sort by i_n of keys that
+// start in position order) / k_slice_gather / k_slice_rowptr order the visit
+// positions by (i_n, position), so the order inside a slice is the visit order,
+// and copy the COO arrays into that order; row_ptr[i] is the first position
+// of slice i.
 //
 // Factor pass (Eq. (9)-(10), element by element as in Algorithm 4).  During a
 // factor pass over mode n a nonzero reads and writes only a_{i_n}; slices are
@@ -42,8 +43,6 @@ namespace sft {
 
 
 // ============================================================================ layout
-constexpr int kSortBlock = 2048;
-
 __global__ void k_slice_keys(const int32_t *__restrict__ rowidx, const uint32_t *__restrict__ perm,
                              int64_t nnz, int32_t In, unsigned long long *__restrict__ keys,
                              int64_t P, int *err) {
@@ -74,42 +73,122 @@ __global__ void k_slice_keys(const int32_t *__restrict__ rowidx, const uint32_t 
     }
 }
 
-// Bitonic stages with partner distance < kSortBlock, in shared memory.  For
-// k_lo == 2 it sorts every block fully (k = 2 .. kSortBlock); otherwise it
-// finishes the merge of size k_lo (== k_hi) from distance kSortBlock/2 down.
-__global__ void __launch_bounds__(kSortBlock / 2) k_bitonic_local(unsigned long long *keys,
-                                                                   int64_t k_lo, int64_t k_hi) {
-    __shared__ unsigned long long s[kSortBlock];
-    const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    s[t] = keys[base + t];
-    s[t + kSortBlock / 2] = keys[base + t + kSortBlock / 2];
-    __syncthreads();
-    for (int64_t k = k_lo; k <= k_hi; k <<= 1) {
-        for (int j = (int)(k / 2 < kSortBlock / 2 ? k / 2 : kSortBlock / 2); j > 0; j >>= 1) {
-            const int i = 2 * j * (t / j) + (t % j);
-            const bool up = ((base + i) & k) == 0;
-            const unsigned long long x = s[i], y = s[i + j];
-            if ((x > y) == up) {
-                s[i] = y;
-                s[i + j] = x;
-            }
-            __syncthreads();
-        }
-    }
-    keys[base + t] = s[t];
-    keys[base + t + kSortBlock / 2] = s[t + kSortBlock / 2];
+// Stable LSD radix sort of the keys by their row (the high 32 bits), 4 bits
+// per pass.  The keys start in position order, so after the passes they are
+// ordered by (row, position): every slice keeps the visit order.  A pass:
+// k_rs_count counts the digits of each tile of kRsTile keys, k_rs_scan turns
+// the counts (digit-major: digit d of every tile, then digit d + 1) into
+// output offsets, and k_rs_scatter moves each tile's keys to their offsets,
+// in order within a digit (the ranks are per-thread counts scanned across
+// the block's threads in thread order, each thread holding consecutive keys).
+constexpr int kRsThreads = 256;
+constexpr int kRsPerThread = 12;
+constexpr int kRsTile = kRsThreads * kRsPerThread;
+constexpr int kRsDigits = 16;
+
+__device__ __forceinline__ int rs_digit(unsigned long long key, int shift) {
+    return (int)((key >> (32 + shift)) & (kRsDigits - 1));
 }
 
-__global__ void k_bitonic_global(unsigned long long *keys, int64_t P, int64_t k, int64_t j) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P / 2; t += stride) {
-        const int64_t i = 2 * j * (t / j) + (t % j);
-        const bool up = (i & k) == 0;
-        const unsigned long long x = keys[i], y = keys[i + j];
-        if ((x > y) == up) {
-            keys[i] = y;
-            keys[i + j] = x;
+__global__ void __launch_bounds__(kRsThreads) k_rs_count(const unsigned long long *__restrict__ in,
+                                                         int64_t n, int shift, int64_t ntiles,
+                                                         unsigned int *__restrict__ hist) {
+    __shared__ unsigned int h[kRsDigits];
+    if (threadIdx.x < kRsDigits) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
+        const int64_t j = base + i;
+        if (j < n) atomicAdd(&h[rs_digit(in[j], shift)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRsDigits) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive prefix sum of m counts in place, one block of 1024 threads (each
+// thread sums a contiguous run, the runs' sums are scanned across the block).
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned int *__restrict__ v, int64_t m) {
+    __shared__ unsigned int part[1024];
+    const int64_t per = (m + 1023) / 1024;
+    const int64_t lo = (int64_t)threadIdx.x * per;
+    const int64_t hi = lo + per < m ? lo + per : m;
+    unsigned int sum = 0;
+    for (int64_t i = lo; i < hi; ++i) sum += v[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+        const unsigned int y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    unsigned int run = part[threadIdx.x] - sum;
+    for (int64_t i = lo; i < hi; ++i) {
+        const unsigned int c = v[i];
+        v[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long long *__restrict__ in,
+                                                           unsigned long long *__restrict__ out,
+                                                           int64_t n, int shift, int64_t ntiles,
+                                                           const unsigned int *__restrict__ offs) {
+    // the tile, padded by one key per thread's run so the runs' reads spread
+    // over the banks; then per digit and thread the count, scanned in place
+    __shared__ unsigned long long sk[kRsTile + kRsThreads];
+    __shared__ unsigned int cnt[kRsDigits][kRsThreads + 1];
+    __shared__ unsigned int goff[kRsDigits];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int i = t; i < kRsTile; i += kRsThreads) {
+        const int64_t j = base + i;
+        sk[i + i / kRsPerThread] = j < n ? in[j] : ~0ull;
+    }
+    for (int d = 0; d < kRsDigits; ++d) cnt[d][t] = 0;
+    if (t < kRsDigits) goff[t] = offs[(int64_t)t * ntiles + blockIdx.x];
+    __syncthreads();
+    const unsigned long long *mine = sk + t * (kRsPerThread + 1);
+    const int64_t first = base + (int64_t)t * kRsPerThread;  // this thread's first key
+#pragma unroll 4
+    for (int i = 0; i < kRsPerThread; ++i)
+        if (first + i < n) cnt[rs_digit(mine[i], shift)][t] += 1u;
+    __syncthreads();
+    // exclusive scan of cnt[d][0..255] for every digit: warp w takes digits
+    // 2w and 2w + 1, each lane a run of 8 threads
+    {
+        const int w = t >> 5, lane = t & 31;
+#pragma unroll
+        for (int dd = 0; dd < 2; ++dd) {
+            const int d = 2 * w + dd;
+            unsigned int c[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = cnt[d][lane * 8 + q];
+                sum += c[q];
+            }
+            unsigned int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            unsigned int run = incl - sum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                cnt[d][lane * 8 + q] = run;
+                run += c[q];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < kRsPerThread; ++i) {
+        if (first + i < n) {
+            const unsigned long long key = mine[i];
+            const int d = rs_digit(key, shift);
+            const unsigned int r = cnt[d][t]++;
+            out[goff[d] + r] = key;
         }
     }
 }
@@ -149,33 +228,41 @@ __global__ void k_slice_rowptr(const unsigned long long *__restrict__ keys, int6
     }
 }
 
+// Scratch of the layout build: two key buffers of nnz and the digit counts
+// of every tile (as unsigned long long units).
 int64_t slice_sort_length(int64_t nnz) {
-    int64_t P = kSortBlock;
-    while (P < nnz) P <<= 1;
-    return P;
+    const int64_t ntiles = (nnz + kRsTile - 1) / kRsTile;
+    return 2 * nnz + (kRsDigits * ntiles + 1) / 2 + 2;
 }
 
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches) {
-    const int64_t P = slice_sort_length(a.nnz);
+    const int64_t n = a.nnz;
     const int th = 256;
-    auto grid = [&](int64_t n) {
-        int64_t b = (n + th - 1) / th;
+    auto grid = [&](int64_t m) {
+        int64_t b = (m + th - 1) / th;
         const int64_t cap = (int64_t)sms * 16;
         return (int)(b < 1 ? 1 : (b > cap ? cap : b));
     };
-    k_slice_keys<<<grid(P), th, 0, st>>>(a.idx[a.n], a.perm, a.nnz, a.dims[a.n], keys, P, a.err);
-    k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, 2, kSortBlock);
-    *launches += 2;
-    for (int64_t k = 2 * kSortBlock; k <= P; k <<= 1) {
-        for (int64_t j = k / 2; j >= kSortBlock; j >>= 1) {
-            k_bitonic_global<<<grid(P / 2), th, 0, st>>>(keys, P, k, j);
-            *launches += 1;
-        }
-        k_bitonic_local<<<(int)(P / kSortBlock), kSortBlock / 2, 0, st>>>(keys, k, k);
-        *launches += 1;
+    unsigned long long *kin = keys, *kout = keys + n;
+    unsigned int *hist = reinterpret_cast<unsigned int *>(keys + 2 * n);
+    const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+    k_slice_keys<<<grid(n), th, 0, st>>>(a.idx[a.n], a.perm, n, a.dims[a.n], kin, n, a.err);
+    *launches += 1;
+    // rows run up to I_n (bad coordinates sort after every slice)
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) <= (int64_t)a.dims[a.n]) ++bits;
+    for (int shift = 0; shift < bits && n > 0; shift += 4) {
+        k_rs_count<<<(int)ntiles, kRsThreads, 0, st>>>(kin, n, shift, ntiles, hist);
+        k_rs_scan<<<1, 1024, 0, st>>>(hist, kRsDigits * ntiles);
+        k_rs_scatter<<<(int)ntiles, kRsThreads, 0, st>>>(kin, kout, n, shift, ntiles, hist);
+        *launches += 3;
+        unsigned long long *tmp = kin;
+        kin = kout;
+        kout = tmp;
     }
+    keys = kin;
     SliceOut o{};
     for (int k = 0; k < a.N; ++k) o.idx[k] = out_idx[k];
     o.val = out_val;
