@@ -21,8 +21,8 @@
 //     and the rest (its map region) split at the tile boundaries.  One step is
 //     the affine map a -> M_t a + c_t with M_t = (1 - lr lambda) I - lr v v^T
 //     and c_t = lr x v, so each piece is composed into one map (M, c) in
-//     parallel (k_slices_maps); k_slices_compose multiplies blocks of
-//     consecutive piece maps and k_slices_combine applies them to the row, in
+//     parallel (k_slices_maps); k_slices_compose_w multiplies blocks of
+//     consecutive piece maps and k_slices_combine_w applies them to the row, in
 //     order, after its head.  This is the same recurrence, re-associated.
 // With the fiber table and J_n <= 16 the interiors and the chains are one
 // work list sorted by length (k_lane_count / k_lane_scatter) that a
@@ -275,11 +275,11 @@ cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, floa
 
 // ============================================================================ long slices: combine
 // Pieces of a long slice (one per tile it touches) are grouped into blocks of
-// Bc = ceil(sqrt(K)) consecutive pieces (K pieces in all).  k_slices_compose
+// Bc = ceil(sqrt(K)) consecutive pieces (K pieces in all).  k_slices_compose_w
 // folds each block into one map, in place in the slot of its first piece
 // (X = P_last; X = X o P for the earlier pieces: X.M <- X.M P.M,
-// X.c <- X.M P.c + X.c), and k_slices_combine applies the block maps to the
-// row in order.  Lane `sub` owns rows [sub*JL, (sub+1)*JL) of X.
+// X.c <- X.M P.c + X.c), and k_slices_combine_w applies the block maps to the
+// row in order.
 
 __device__ __forceinline__ int64_t block_len(int64_t K) {
     int64_t b = (int64_t)sqrtf((float)K);
@@ -299,248 +299,224 @@ __device__ __forceinline__ bool long_piece(const SliceArgs &g, int64_t t, int si
     return map_piece(g, t, side, r, s, e, hs, q0, q1);
 }
 
-constexpr int kComposeGroups = 8;  // lane groups per block of k_slices_compose
+// ---------------------------------------------------------------------------- one warp per chain
+// The block products of the composition and the block-map applications are
+// sequential chains; the longest chain (the longest
+// slice: Bc = ceil(sqrt(K)) products, K up to ~1e4 pieces on a Zipf mode)
+// sets their time.  These forms give each chain a whole warp, taken from
+// lists built by k_long_list (every long slice, and every block start of its
+// map region), so a product or an application is short and no warp idles on
+// the tiles that start no block.  The arithmetic (each entry's sums in
+// ascending order) is that of the lane-group forms, bit for bit.
 
-// Form for J = 32 or lanes holding more than 4 rows (J/T > 4).  X (the running block map,
-// rows of X.M then X.c) lives in shared memory; lane
-// `sub` owns columns [sub*JL, (sub+1)*JL) of X.M and rows [sub*JL, ...) of X.c.
-// Each product X <- X o P first pulls the lane's column slice of P.M and all of
-// P.c into registers (one memory latency per product), then computes the new
-// columns from the whole of X; a group barrier separates reads from writes.
-template <int R, int J>
-__global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose_smem(SliceArgs g) {
-    constexpr int T = R / 4;
-    constexpr int JL = J / T;
-    constexpr int MS = J * J + J;
-    __shared__ __align__(16) float sX[kComposeGroups * MS];
-    const int sub = threadIdx.x & (T - 1);
-    const int gid = threadIdx.x / T;
-    const unsigned m = group_mask<T>(threadIdx.x & 31);
-    float *X = sX + gid * MS;
-    const int64_t groups = (int64_t)gridDim.x * kComposeGroups;
-    for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
-        for (int side = 0; side < 2; ++side) {
-            int32_t r;
-            int64_t s, e, hs;
-            if (!long_piece(g, t, side, r, s, e, hs)) continue;
-            const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
-            const int64_t Bc = block_len(t1 - t0 + 1);
-            if ((t - t0) % Bc != 0) continue;
-            const int64_t tl = min(t + Bc - 1, t1);
-            if (tl == t) continue;  // a block of one piece is already its own map
-            const float *P = g.maps + (tl * 2 + piece_slot(hs, tl, g.W)) * (int64_t)MS;
-            for (int j = 0; j < J; ++j)
-#pragma unroll
-                for (int q = 0; q < JL; ++q) X[j * J + sub * JL + q] = __ldcg(P + j * J + sub * JL + q);
-#pragma unroll
-            for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = __ldcg(P + J * J + sub * JL + q);
-            __syncwarp(m);
-            for (int64_t u = tl - 1; u >= t; --u) {
-                P = g.maps + (u * 2 + piece_slot(hs, u, g.W)) * (int64_t)MS;
-                float pc[J];          // all of P.c
-                float pm[J][JL];      // the lane's columns of P.M
-#pragma unroll
-                for (int l = 0; l < J; ++l) {
-                    pc[l] = __ldcg(P + J * J + l);
-#pragma unroll
-                    for (int q = 0; q < JL; ++q) pm[l][q] = __ldcg(P + l * J + sub * JL + q);
-                }
-                // new X.c for the lane's rows (reads rows of the old X.M)
-                float nc[JL];
-#pragma unroll
-                for (int q = 0; q < JL; ++q) {
-                    const int j = sub * JL + q;
-                    float acc = X[J * J + j];
-#pragma unroll
-                    for (int l = 0; l < J; ++l) acc = fmaf(X[j * J + l], pc[l], acc);
-                    nc[q] = acc;
-                }
-                // one row of X.M at a time: read it whole, then write the lane's columns
-#pragma unroll 1
-                for (int j = 0; j < J; ++j) {
-                    float nrow[JL];
-#pragma unroll
-                    for (int q = 0; q < JL; ++q) nrow[q] = 0.f;
-#pragma unroll
-                    for (int l = 0; l < J; ++l) {
-                        const float xjl = X[j * J + l];
-#pragma unroll
-                        for (int q = 0; q < JL; ++q) nrow[q] = fmaf(xjl, pm[l][q], nrow[q]);
-                    }
-                    __syncwarp(m);
-#pragma unroll
-                    for (int q = 0; q < JL; ++q) X[j * J + sub * JL + q] = nrow[q];
-                    __syncwarp(m);
-                }
-#pragma unroll
-                for (int q = 0; q < JL; ++q) X[J * J + sub * JL + q] = nc[q];
-                __syncwarp(m);
-            }
-            float *out = g.maps + (t * 2 + piece_slot(hs, t, g.W)) * (int64_t)MS;
-            for (int j = 0; j < J; ++j)
-#pragma unroll
-                for (int q = 0; q < JL; ++q) out[j * J + sub * JL + q] = X[j * J + sub * JL + q];
-#pragma unroll
-            for (int q = 0; q < JL; ++q) out[J * J + sub * JL + q] = X[J * J + sub * JL + q];
-            __syncwarp(m);
-        }
+// Lane layout of a J x J map over one warp: LPR lanes per row, CPL columns
+// per lane (J = 4 uses 16 lanes).
+template <int J>
+struct WarpMap {
+    static constexpr int LPR = (32 / J) < J ? (32 / J) : J;
+    static constexpr int CPL = J / LPR;
+    static constexpr int LANES = J * LPR;
+};
+constexpr int kWarpMapWarps = 4;   // warps per block of the warp-per-chain kernels
+constexpr int kCombineRing = 4;    // block maps staged ahead by k_slices_combine_w (J <= 16)
+
+// The long slices of the pass (rows, into longs) and the block starts of their
+// map regions (t * 2 + slot, into starts).  counts[0] / counts[1] receive the
+// two lengths.
+__global__ void k_long_list(SliceArgs g, int32_t *longs, int32_t *starts, unsigned int *counts) {
+    const int32_t In = g.a.dims[g.a.n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < In;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g.row_ptr[r], e = g.row_ptr[r + 1];
+        if (s < 0 || s >= e || e > g.a.nnz) continue;
+        if (e - s <= g.Lseq || s / g.W == (e - 1) / g.W) continue;  // not long / not crossing
+        const int64_t hs = s + g.Lhead;
+        if (hs >= e) continue;
+        longs[atomicAdd(&counts[0], 1u)] = (int32_t)r;
+        const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
+        const int64_t Bc = block_len(t1 - t0 + 1);
+        for (int64_t t = t0; t <= t1; t += Bc)
+            if (min(t + Bc - 1, t1) > t)  // a block of one piece is already its own map
+                starts[atomicAdd(&counts[1], 1u)] = (int32_t)(t * 2 + piece_slot(hs, t, g.W));
     }
 }
 
-// Form for J <= 16 and J/T <= 4.  X (the running block map) lives in registers: lane `sub` holds rows
-// [sub*JL, (sub+1)*JL) of X.M and of X.c.  The group stages each piece map P in
-// shared memory with cp.async, two buffers deep (the next P is in flight while
-// the current product runs); every lane reads P whole (broadcast) and forms its
-// rows of X o P:  X.M <- X.M P.M,  X.c <- X.M P.c + X.c, each entry summed
-// over l in ascending order.
-template <int R, int J>
-__global__ void __launch_bounds__(kComposeGroups * (R / 4)) k_slices_compose(SliceArgs g) {
-    constexpr int T = R / 4;
-    constexpr int JL = J / T;
+template <int J>
+__global__ void __launch_bounds__(kWarpMapWarps * 32) k_slices_compose_w(SliceArgs g,
+                                                                       const int32_t *starts,
+                                                                       const unsigned int *count) {
+    using WM = WarpMap<J>;
     constexpr int MS = J * J + J;
     constexpr int CH = MS / 4;  // 16-byte chunks of one map
-    __shared__ __align__(16) float sP[kComposeGroups * 2 * MS];
-    const int sub = threadIdx.x & (T - 1);
-    const int gid = threadIdx.x / T;
-    const unsigned m = group_mask<T>(threadIdx.x & 31);
-    float *buf = sP + gid * 2 * MS;
+    constexpr int CPL = WM::CPL;
+    __shared__ __align__(16) float sP[kWarpMapWarps][2][MS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane / WM::LPR, part = lane % WM::LPR, c0 = part * CPL;
+    const bool act = lane < WM::LANES;
+    const int rbase = lane - part;  // first lane of this lane's row
+    const int64_t n = (int64_t)*count;
     auto stage = [&](const float *P, float *dst) {
-        for (int c = sub; c < CH; c += T) {
+        for (int c = lane; c < CH; c += 32) {
             const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 4 * c));
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(P + 4 * c)
                          : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    const int64_t groups = (int64_t)gridDim.x * kComposeGroups;
-    for (int64_t t = (int64_t)blockIdx.x * kComposeGroups + gid; t < g.ntiles; t += groups) {
-        for (int side = 0; side < 2; ++side) {
-            int32_t r;
-            int64_t s, e, hs;
-            if (!long_piece(g, t, side, r, s, e, hs)) continue;
-            const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
-            const int64_t Bc = block_len(t1 - t0 + 1);
-            if ((t - t0) % Bc != 0) continue;
-            const int64_t tl = min(t + Bc - 1, t1);
-            if (tl == t) continue;  // a block of one piece is already its own map
-            auto map_of = [&](int64_t u) {
-                return g.maps + (u * 2 + piece_slot(hs, u, g.W)) * (int64_t)MS;
-            };
-            stage(map_of(tl - 1), buf);
-            float X[JL][J], Xc[JL];
-            {
-                const float *P = map_of(tl);
+    for (int64_t k = (int64_t)blockIdx.x * kWarpMapWarps + warp; k < n;
+         k += (int64_t)gridDim.x * kWarpMapWarps) {
+        const int32_t entry = starts[k];
+        const int64_t t = entry >> 1;
+        const int side = entry & 1;
+        int32_t row;
+        int64_t s, e, hs;
+        if (t >= g.ntiles || !long_piece(g, t, side, row, s, e, hs)) continue;
+        const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
+        const int64_t Bc = block_len(t1 - t0 + 1);
+        const int64_t tl = min(t + Bc - 1, t1);
+        if (tl == t || (t - t0) % Bc != 0) continue;
+        auto map_of = [&](int64_t u) {
+            return g.maps + (u * 2 + piece_slot(hs, u, g.W)) * (int64_t)MS;
+        };
+        stage(map_of(tl - 1), sP[warp][0]);
+        // X = the last piece's map; every lane of a row holds the whole row
+        float X[J], Xc = 0.f;
+        {
+            const float *P = map_of(tl);
 #pragma unroll
-                for (int q = 0; q < JL; ++q) {
-#pragma unroll
-                    for (int k = 0; k < J; k += 4) {
-                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(
-                            P + (sub * JL + q) * J + k));
-                        X[q][k] = v.x; X[q][k + 1] = v.y; X[q][k + 2] = v.z; X[q][k + 3] = v.w;
-                    }
-                    Xc[q] = __ldcg(P + J * J + sub * JL + q);
-                }
+            for (int l = 0; l < J; l += 4) {
+                const float4 v = act ? __ldcg(reinterpret_cast<const float4 *>(P + r * J + l))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                X[l] = v.x; X[l + 1] = v.y; X[l + 2] = v.z; X[l + 3] = v.w;
             }
-            int cur = 0;
-            for (int64_t u = tl - 1; u >= t; --u) {
-                if (u > t) {
-                    stage(map_of(u - 1), buf + (cur ^ 1) * MS);
-                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+            if (act) Xc = __ldcg(P + J * J + r);
+        }
+        int cur = 0;
+        for (int64_t u = tl - 1; u >= t; --u) {
+            if (u > t) {
+                stage(map_of(u - 1), sP[warp][cur ^ 1]);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncwarp();  // every lane's chunks of P have landed
+            const float *P = sP[warp][cur];
+            // X <- X o P on the lane's columns: X.M <- X.M P.M, X.c <- X.M P.c + X.c
+            float nx[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) nx[q] = 0.f;
+            float acc = Xc;
+#pragma unroll
+            for (int l = 0; l < J; ++l) {
+                const float x = X[l];
+                if constexpr (CPL % 4 == 0) {
+#pragma unroll
+                    for (int q = 0; q < CPL; q += 4) {
+                        const float4 pv = *reinterpret_cast<const float4 *>(P + l * J + c0 + q);
+                        nx[q] = fmaf(x, pv.x, nx[q]);
+                        nx[q + 1] = fmaf(x, pv.y, nx[q + 1]);
+                        nx[q + 2] = fmaf(x, pv.z, nx[q + 2]);
+                        nx[q + 3] = fmaf(x, pv.w, nx[q + 3]);
+                    }
                 } else {
-                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) nx[q] = fmaf(x, P[l * J + c0 + q], nx[q]);
                 }
-                __syncwarp(m);  // every lane's chunks of P have landed
-                const float *P = buf + cur * MS;
-#pragma unroll
-                for (int q = 0; q < JL; ++q) {
-                    float nrow[J];
-#pragma unroll
-                    for (int k = 0; k < J; ++k) nrow[k] = 0.f;
-                    float acc = Xc[q];
-#pragma unroll
-                    for (int l = 0; l < J; ++l) {
-                        const float x = X[q][l];
-#pragma unroll
-                        for (int k = 0; k < J; k += 4) {
-                            const float4 pv = *reinterpret_cast<const float4 *>(P + l * J + k);
-                            nrow[k] = fmaf(x, pv.x, nrow[k]);
-                            nrow[k + 1] = fmaf(x, pv.y, nrow[k + 1]);
-                            nrow[k + 2] = fmaf(x, pv.z, nrow[k + 2]);
-                            nrow[k + 3] = fmaf(x, pv.w, nrow[k + 3]);
-                        }
-                        acc = fmaf(x, P[J * J + l], acc);
-                    }
-#pragma unroll
-                    for (int k = 0; k < J; ++k) X[q][k] = nrow[k];
-                    Xc[q] = acc;
-                }
-                __syncwarp(m);  // P fully read before its buffer is refilled
-                cur ^= 1;
+                acc = fmaf(x, P[J * J + l], acc);
             }
+            __syncwarp();  // P fully read before its buffer is refilled
+            // the whole new row back into every lane of the row
+#pragma unroll
+            for (int j = 0; j < J; ++j) X[j] = __shfl_sync(0xffffffffu, nx[j % CPL], rbase + j / CPL);
+            Xc = acc;
+            cur ^= 1;
+        }
+        if (act) {
             float *out = map_of(t);
 #pragma unroll
-            for (int q = 0; q < JL; ++q) {
-#pragma unroll
-                for (int k = 0; k < J; k += 4)
-                    *reinterpret_cast<float4 *>(out + (sub * JL + q) * J + k) =
-                        make_float4(X[q][k], X[q][k + 1], X[q][k + 2], X[q][k + 3]);
-                out[J * J + sub * JL + q] = Xc[q];
-            }
+            for (int j = 0; j < J; ++j)  // the lane's columns (no run-time register index)
+                if (j / CPL == part) out[r * J + j] = X[j];
+            if (part == 0) out[J * J + r] = Xc;
         }
+        __syncwarp();
     }
 }
 
-template <int R, int J>
-__global__ void __launch_bounds__(kSliceThreads) k_slices_combine(SliceArgs g) {
-    constexpr int T = R / 4;
-    constexpr int JL = J / T;
+// Applies the block maps of each long slice's map region, in order, to the
+// row its head left: lane j < J forms entry j (c_j, then the row's dot product
+// in ascending order), the block maps staged kCombineRing ahead with cp.async.
+template <int J>
+__global__ void __launch_bounds__(kWarpMapWarps * 32) k_slices_combine_w(SliceArgs g,
+                                                                       const int32_t *longs,
+                                                                       const unsigned int *count) {
     constexpr int MS = J * J + J;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (T - 1);
-    const unsigned m = group_mask<T>(lane);
-    const int64_t groups = (int64_t)gridDim.x * (kSliceThreads / T);
-    for (int64_t item = (int64_t)blockIdx.x * (kSliceThreads / T) + threadIdx.x / T;
-         item < g.ntiles - 1; item += groups) {
-        int32_t r;
-        int64_t s, e;
-        if (!first_boundary_slice(g, item + 1, r, s, e) || e - s <= g.Lseq) continue;
-        // the row after the slice's head (run by the chain kernel), then the
-        // block maps of its map region [hs, e) in order
-        float *arow = g.a.A + (int64_t)r * J + sub * JL;
-        float av[JL];
-        load_run<JL>(arow, av);
+    constexpr int CH = MS / 4;
+    constexpr int D = J <= 16 ? kCombineRing : 2;
+    __shared__ __align__(16) float sM[kWarpMapWarps][D][MS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = (int64_t)*count;
+    for (int64_t k = (int64_t)blockIdx.x * kWarpMapWarps + warp; k < n;
+         k += (int64_t)gridDim.x * kWarpMapWarps) {
+        const int32_t r = longs[k];
+        if (r < 0 || r >= g.a.dims[g.a.n]) continue;
+        const int64_t s = __ldg(g.row_ptr + r), e = __ldg(g.row_ptr + r + 1);
+        if (!slice_ok(g, s, e)) continue;
         const int64_t hs = s + g.Lhead;
         const int64_t t0 = hs / g.W, t1 = (e - 1) / g.W;
         const int64_t Bc = block_len(t1 - t0 + 1);
-        for (int64_t t = t0; t <= t1; t += Bc) {
-            const float *mp = g.maps + (t * 2 + piece_slot(hs, t, g.W)) * (int64_t)MS;
-            float full[J];
-#pragma unroll
-            for (int k = 0; k < J; ++k) full[k] = __shfl_sync(m, av[k % JL], k / JL, T);
-#pragma unroll
-            for (int q = 0; q < JL; ++q) {
-                const float *row = mp + (sub * JL + q) * J;
-                float acc = __ldcg(mp + J * J + sub * JL + q);
-#pragma unroll
-                for (int k4 = 0; k4 < J / 4; ++k4) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(row) + k4);
-                    acc = fmaf(v.x, full[4 * k4], acc);
-                    acc = fmaf(v.y, full[4 * k4 + 1], acc);
-                    acc = fmaf(v.z, full[4 * k4 + 2], acc);
-                    acc = fmaf(v.w, full[4 * k4 + 3], acc);
+        const int64_t nb = (t1 - t0) / Bc + 1;  // block maps, at t0, t0 + Bc, ...
+        auto map_of = [&](int64_t b) {
+            const int64_t t = t0 + b * Bc;
+            return g.maps + (t * 2 + piece_slot(hs, t, g.W)) * (int64_t)MS;
+        };
+        auto stage = [&](int64_t b) {
+            if (b < nb) {
+                const float *P = map_of(b);
+                float *dst = sM[warp][b % D];
+                for (int c = lane; c < CH; c += 32) {
+                    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 4 * c));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                                 "l"(P + 4 * c)
+                                 : "memory");
                 }
-                av[q] = acc;
             }
-        }
-        if constexpr (JL >= 4) {
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        float *arow = g.a.A + (int64_t)r * J;
+        float a[J];
 #pragma unroll
-            for (int q = 0; q < JL / 4; ++q)
-                *reinterpret_cast<float4 *>(arow + 4 * q) =
-                    make_float4(av[4 * q], av[4 * q + 1], av[4 * q + 2], av[4 * q + 3]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < JL; ++q) arow[q] = av[q];
+        for (int l = 0; l < J; l += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(arow + l);
+            a[l] = v.x; a[l + 1] = v.y; a[l + 2] = v.z; a[l + 3] = v.w;
         }
+        for (int64_t b = 0; b < D - 1; ++b) stage(b);
+        for (int64_t b = 0; b < nb; ++b) {
+            stage(b + D - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(D - 1) : "memory");
+            __syncwarp();  // block map b has landed
+            const float *M = sM[warp][b % D];
+            float acc = 0.f;
+            if (lane < J) {
+                acc = M[J * J + lane];
+#pragma unroll
+                for (int l = 0; l < J; l += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(M + lane * J + l);
+                    acc = fmaf(v.x, a[l], acc);
+                    acc = fmaf(v.y, a[l + 1], acc);
+                    acc = fmaf(v.z, a[l + 2], acc);
+                    acc = fmaf(v.w, a[l + 3], acc);
+                }
+            }
+            __syncwarp();  // map b read before its slot is refilled
+#pragma unroll
+            for (int l = 0; l < J; ++l) a[l] = __shfl_sync(0xffffffffu, acc, l);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l < J; ++l)  // lane l writes entry l (no run-time register index)
+            if (lane == l) arow[l] = a[l];
+        __syncwarp();
     }
 }
 
@@ -727,8 +703,8 @@ size_t slice_maps_bytes(int64_t ntiles, int J) {
 
 // Workspace of a slice factor pass: the piece maps, the chain list (a count
 // and one row per tile), the piece list (two counts and two entries per
-// tile), then the one-lane work list, each part starting on a 16-byte
-// boundary.
+// tile), the combine lists, then the one-lane work list, each part starting
+// on a 16-byte boundary.
 size_t slice_chain_list_offset(int64_t ntiles, int J) { return slice_maps_bytes(ntiles, J); }
 
 size_t slice_piece_list_offset(int64_t ntiles, int J) {
@@ -736,8 +712,15 @@ size_t slice_piece_list_offset(int64_t ntiles, int J) {
     return (o + 15) / 16 * 16;
 }
 
-size_t slice_lane_list_offset(int64_t ntiles, int J) {
+// The combine lists: two counts, then a row per long slice (at most one per
+// tile boundary) and a block start per piece (at most two per tile).
+size_t slice_combine_list_offset(int64_t ntiles, int J) {
     const size_t o = slice_piece_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 2 * 4;
+    return (o + 15) / 16 * 16;
+}
+
+size_t slice_lane_list_offset(int64_t ntiles, int J) {
+    const size_t o = slice_combine_list_offset(ntiles, J) + 16 + (size_t)(ntiles < 1 ? 1 : ntiles) * 3 * 4;
     return (o + 15) / 16 * 16;
 }
 
@@ -850,21 +833,34 @@ cudaError_t launch_factor_slices(const PassArgs &a, const int32_t *row_ptr, int6
 // Compose the piece maps of long slices in blocks, then apply them in order
 // to the rows (after the map kernel has finished).
 cudaError_t launch_slice_combine(const SliceArgs &g, int J, int R, cudaStream_t st, int sms) {
-    dispatch_rj(R, J, [&](auto r_c, auto j_c) {
-        constexpr int R_ = decltype(r_c)::value, J_ = decltype(j_c)::value;
-        const int gpb = kSliceThreads / (R_ / 4);
-        const int cth = kComposeGroups * (R_ / 4);
-        if constexpr (J_ <= 16 && J_ / (R_ / 4) <= 4) {
-            const int gc = grid_for(k_slices_compose<R_, J_>, cth, 0, kComposeGroups, g.ntiles, sms);
-            k_slices_compose<R_, J_><<<gc, cth, 0, st>>>(g);
-        } else {
-            const int gc = grid_for(k_slices_compose_smem<R_, J_>, cth, 0, kComposeGroups, g.ntiles,
-                                    sms);
-            k_slices_compose_smem<R_, J_><<<gc, cth, 0, st>>>(g);
-        }
-        const int gb = grid_for(k_slices_combine<R_, J_>, kSliceThreads, 0, gpb, g.ntiles, sms);
-        k_slices_combine<R_, J_><<<gb, kSliceThreads, 0, st>>>(g);
-    });
+    (void)R;
+    char *base = (char *)g.maps + slice_combine_list_offset(g.ntiles, J);
+    unsigned int *counts = (unsigned int *)base;
+    int32_t *longs = (int32_t *)(base + 16);
+    int32_t *starts = longs + (g.ntiles < 1 ? 1 : g.ntiles);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const int32_t In = g.a.dims[g.a.n];
+    int64_t lb = ((int64_t)In + 255) / 256;
+    if (lb > (int64_t)sms * 4) lb = (int64_t)sms * 4;
+    if (lb < 1) lb = 1;
+    k_long_list<<<(int)lb, 256, 0, st>>>(g, longs, starts, counts);
+    auto run = [&](auto j_c) {
+        constexpr int J_ = decltype(j_c)::value;
+        const int gc = grid_for(k_slices_compose_w<J_>, kWarpMapWarps * 32, 0, kWarpMapWarps,
+                                (int64_t)1 << 30, sms);
+        k_slices_compose_w<J_><<<gc, kWarpMapWarps * 32, 0, st>>>(g, starts, counts + 1);
+        const int gb = grid_for(k_slices_combine_w<J_>, kWarpMapWarps * 32, 0, kWarpMapWarps,
+                                (int64_t)1 << 30, sms);
+        k_slices_combine_w<J_><<<gb, kWarpMapWarps * 32, 0, st>>>(g, longs, counts);
+    };
+    switch (J) {
+        case 4: run(ic<4>{}); break;
+        case 8: run(ic<8>{}); break;
+        case 16: run(ic<16>{}); break;
+        case 32: run(ic<32>{}); break;
+        default: break;
+    }
     return cudaGetLastError();
 }
 

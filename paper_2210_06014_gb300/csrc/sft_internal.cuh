@@ -85,6 +85,7 @@ int64_t slice_sort_length(int64_t nnz);
 size_t slice_maps_bytes(int64_t ntiles, int J);
 size_t slice_chain_list_offset(int64_t ntiles, int J);
 size_t slice_piece_list_offset(int64_t ntiles, int J);
+size_t slice_combine_list_offset(int64_t ntiles, int J);
 size_t slice_lane_list_offset(int64_t ntiles, int J);
 size_t slice_workspace_total(int64_t ntiles, int J, int64_t In);
 // the fiber factor pass runs its tiles and short chains with the one-lane
