@@ -153,7 +153,10 @@ __global__ void k_core_apply(float *__restrict__ B, const float *__restrict__ pa
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= JR) return;
     double g = 0.0;
-    for (int b = 0; b < nblk; ++b) g += (double)partials[(int64_t)b * JR + q];
+    // the same sum in block order; unrolled so that the partials' loads are in
+    // flight together instead of one latency per block
+#pragma unroll 16
+    for (int b = 0; b < nblk; ++b) g += (double)__ldg(partials + (int64_t)b * JR + q);
     const double bq = B[q];
     B[q] = (float)(bq + (double)lr * (g / (double)Mb - (double)lam * bq));
 }

@@ -68,64 +68,76 @@ cudaError_t launch_refresh(const float *A, const float *B, float *C, int64_t I, 
 // the result is bitwise reproducible for a given grid size.
 constexpr int kLossThreads = 256;
 
-template <int R, typename CT>
+// NO: a compile-time bound on the order (the rows of a nonzero are held in
+// registers, NO float4 per lane).  A group's nonzeros are a two-level
+// pipeline: the coordinates of the nonzero after next and the cached rows of
+// the next one are in flight while the current one is formed.
+template <int R, typename CT, int NO>
 __global__ void __launch_bounds__(kLossThreads) k_loss(PassArgs a, double *__restrict__ partials) {
     constexpr int T = R / 4;
     constexpr int GPW = 32 / T;
     constexpr int WARPS = kLossThreads / 32;
+    constexpr int64_t STEP = (int64_t)WARPS * GPW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (T - 1), gw = lane / T;
     const int64_t span = (a.count + gridDim.x - 1) / gridDim.x;
     const int64_t p0 = (int64_t)blockIdx.x * span;
     const int64_t p1 = min(a.count, p0 + span);
     double s2 = 0.0, s1 = 0.0;
-    // the coordinates and value of the group's next nonzero are loaded one
-    // iteration ahead, so the row gathers of a nonzero never wait on them
-    struct Next {
-        int32_t ik[kMaxOrder];
+    struct Coords {
+        int32_t ik[NO];
         float x;
         bool ok;
     };
-    auto fetch = [&](int64_t pos, Next &nx) {
+    struct Rows {
+        float4 c[NO];
+        float x;
+        bool ok;
+    };
+    auto fetch = [&](int64_t pos, Coords &nx) {
         nx.ok = pos < p1;
         int64_t s = 0;
         if (nx.ok) nx.ok = sample_at(a, a.base + pos, s);
 #pragma unroll
-        for (int k = 0; k < kMaxOrder; ++k) nx.ik[k] = (nx.ok && k < a.N) ? __ldg(a.idx[k] + s) : 0;
+        for (int k = 0; k < NO; ++k) nx.ik[k] = (nx.ok && k < a.N) ? __ldg(a.idx[k] + s) : 0;
         nx.x = nx.ok ? __ldg(a.val + s) : 0.f;
     };
-    Next cur;
-    fetch(p0 + (int64_t)warp * GPW + gw, cur);
-    for (int64_t t0 = p0 + (int64_t)warp * GPW; t0 < p1; t0 += (int64_t)WARPS * GPW) {
-        Next nx;
-        fetch(t0 + (int64_t)WARPS * GPW + gw, nx);
-        bool ok = cur.ok;
-        int32_t ik[kMaxOrder];
+    // checks a nonzero's coordinates (they have arrived) and issues its row gathers
+    auto gather = [&](const Coords &cd, Rows &rw) {
+        bool ok = cd.ok;
 #pragma unroll
-        for (int k = 0; k < kMaxOrder; ++k) {
-            ik[k] = cur.ik[k];
-            if (ok && k < a.N && (uint32_t)ik[k] >= (uint32_t)a.dims[k]) {
+        for (int k = 0; k < NO; ++k)
+            if (ok && k < a.N && (uint32_t)cd.ik[k] >= (uint32_t)a.dims[k]) {
                 atomicOr(a.err, kErrIndex);
                 ok = false;
             }
-        }
-        float4 p = make_float4(ok ? 1.f : 0.f, ok ? 1.f : 0.f, ok ? 1.f : 0.f, ok ? 1.f : 0.f);
-        const float x = ok ? cur.x : 0.f;
 #pragma unroll
-        for (int k0 = 0; k0 < kMaxOrder; k0 += 4) {
-            if (k0 < a.N) {
-                float4 c[4];
+        for (int k = 0; k < NO; ++k)
+            rw.c[k] = (ok && k < a.N) ? ldC<CT>(a.C[k], (int64_t)cd.ik[k] * R + 4 * sub)
+                                      : make_float4(1.f, 1.f, 1.f, 1.f);
+        rw.ok = ok;
+        rw.x = ok ? cd.x : 0.f;
+    };
+    const int64_t q0 = p0 + (int64_t)warp * GPW + gw;
+    Coords c1, c2;
+    Rows cur;
+    fetch(q0, c1);
+    fetch(q0 + STEP, c2);
+    gather(c1, cur);
+    for (int64_t t0 = p0 + (int64_t)warp * GPW; t0 < p1; t0 += STEP) {
+        const int64_t q = t0 + gw;
+        Coords c3;
+        fetch(q + 2 * STEP, c3);
+        Rows nx;
+        gather(c2, nx);
+        float4 p = make_float4(cur.ok ? 1.f : 0.f, cur.ok ? 1.f : 0.f, cur.ok ? 1.f : 0.f,
+                               cur.ok ? 1.f : 0.f);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = k0 + u;
-                    c[u] = (ok && k < a.N) ? ldC<CT>(a.C[k], (int64_t)ik[k] * R + 4 * sub)
-                                           : make_float4(1.f, 1.f, 1.f, 1.f);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) mul4(p, c[u]);
-            }
-        }
+        for (int k = 0; k < NO; ++k) mul4(p, cur.c[k]);
+        const bool ok = cur.ok;
+        const float x = cur.x;
         cur = nx;
+        c2 = c3;
         const float xh = group_sum<T>((p.x + p.y) + (p.z + p.w));
         if (ok && sub == 0) {
             const double e = (double)x - (double)xh;
@@ -185,10 +197,17 @@ int loss_blocks_for(int64_t count, int sms) {
 
 cudaError_t launch_loss(const PassArgs &a, int R, double *partials, int nblk, double *out2,
                         cudaStream_t st) {
-    if (a.cbf16)
-        SFT_DISPATCH_R(R, (k_loss<R_, __nv_bfloat16><<<nblk, kLossThreads, 0, st>>>(a, partials)));
-    else
-        SFT_DISPATCH_R(R, (k_loss<R_, float><<<nblk, kLossThreads, 0, st>>>(a, partials)));
+    auto run = [&](auto no_c) {
+        constexpr int NO = decltype(no_c)::value;
+        if (a.cbf16)
+            SFT_DISPATCH_R(R, (k_loss<R_, __nv_bfloat16, NO><<<nblk, kLossThreads, 0, st>>>(a, partials)));
+        else
+            SFT_DISPATCH_R(R, (k_loss<R_, float, NO><<<nblk, kLossThreads, 0, st>>>(a, partials)));
+    };
+    if (a.N <= 3) run(ic<3>{});
+    else if (a.N <= 4) run(ic<4>{});
+    else if (a.N <= 8) run(ic<8>{});
+    else run(ic<kMaxOrder>{});
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_loss_final<<<1, 32, 0, st>>>(partials, nblk, out2);
