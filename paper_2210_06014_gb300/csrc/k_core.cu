@@ -11,7 +11,7 @@
 // them into a warp-private G tile with FFMA (lane = column r, a run of rows).
 // A block owns a contiguous span of the minibatch and writes one partial tile;
 // everything is summed in a fixed order, so results are bitwise reproducible.
-// Kernel 2 (k_core_apply): sums the block partials in block order (float64)
+// Kernel 2 (k_core_apply): sums the block partials in a fixed order (float64)
 // and applies B += lr (G / M_b - lambda B).
 //
 // This CUDA-core form is exact in float32 (the float32 parity mode).  With
@@ -148,17 +148,35 @@ __global__ void __launch_bounds__(kCoreThreads) k_core_grad(PassArgs a, float *_
     }
 }
 
-__global__ void k_core_apply(float *__restrict__ B, const float *__restrict__ partials, int nblk,
-                             int JR, int64_t Mb, float lr, float lam) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= JR) return;
+// B += lr (G / M_b - lambda B) with G the sum of the block partials.  A block
+// takes 32 entries of G; warp w sums, in float64, the partials of blocks
+// w, w + 8, w + 16, ... (lane l: entry l, so the loads are coalesced), and the
+// eight warp sums are added in warp order: a fixed order for a given partial
+// count, spread over several SMs (one SM's float64 rate made a single-block
+// sum of 608 partials take ~90 us).
+constexpr int kApplyWarps = 8;
+
+__global__ void __launch_bounds__(kApplyWarps * 32) k_core_apply(float *__restrict__ B,
+                                                              const float *__restrict__ partials,
+                                                              int nblk, int JR, int64_t Mb,
+                                                              float lr, float lam) {
+    __shared__ double part[kApplyWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
     double g = 0.0;
-    // the same sum in block order; unrolled so that the partials' loads are in
-    // flight together instead of one latency per block
-#pragma unroll 16
-    for (int b = 0; b < nblk; ++b) g += (double)__ldg(partials + (int64_t)b * JR + q);
-    const double bq = B[q];
-    B[q] = (float)(bq + (double)lr * (g / (double)Mb - (double)lam * bq));
+    if (q < JR) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += kApplyWarps) g += (double)__ldg(partials + (int64_t)b * JR + q);
+    }
+    part[w][lane] = g;
+    __syncthreads();
+    if (w == 0 && q < JR) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kApplyWarps; ++k) t += part[k][lane];
+        const double bq = B[q];
+        B[q] = (float)(bq + (double)lr * (t / (double)Mb - (double)lam * bq));
+    }
 }
 
 // One block per 128 nonzeros (a 4096-nonzero minibatch spreads over 32 SMs),
@@ -181,7 +199,7 @@ cudaError_t launch_core(const PassArgs &a, int J, int R, float *partials, int nb
 
 cudaError_t launch_core_apply(float *B, const float *partials, int nblk, int JR, int64_t Mb,
                               float lr, float lam, cudaStream_t st) {
-    k_core_apply<<<(JR + 255) / 256, 256, 0, st>>>(B, partials, nblk, JR, Mb, lr, lam);
+    k_core_apply<<<(JR + 31) / 32, kApplyWarps * 32, 0, st>>>(B, partials, nblk, JR, Mb, lr, lam);
     return cudaGetLastError();
 }
 

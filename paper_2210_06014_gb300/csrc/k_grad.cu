@@ -19,7 +19,7 @@
 //   k_grad_project  per mode: gA = s dC B^T row by row, and block partials of
 //                 gB = s A^T dC.  A and dC tiles are staged in shared memory;
 //                 s is the incoming gradient of L, read on the device.
-//   k_grad_reduce   sums the gB partials in block order (float64).
+//   k_grad_reduce   sums the gB partials in a fixed order (float64).
 // Without dC buffers k_loss_grad computes only the loss.
 #include "dispatch.cuh"
 #include "sft_internal.cuh"
@@ -252,13 +252,32 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_project(const float *__re
     }
 }
 
-__global__ void k_grad_reduce(const float *__restrict__ partials, int nblk, int JR,
-                              const double *__restrict__ scale, float *__restrict__ gB) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= JR) return;
+// A block takes 32 entries of dL/dB; warp w sums (float64) the partials of
+// blocks w, w + 8, ... (lane l: entry l), then the warp sums are added in warp
+// order: a fixed order, spread over JR / 32 SMs instead of one SM's float64
+// units.
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(kReduceWarps * 32) k_grad_reduce(const float *__restrict__ partials,
+                                                                int nblk, int JR,
+                                                                const double *__restrict__ scale,
+                                                                float *__restrict__ gB) {
+    __shared__ double part[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
     double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += (double)partials[(int64_t)b * JR + q];
-    gB[q] = (float)((scale ? *scale : 1.0) * t);
+    if (q < JR) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += kReduceWarps) t += (double)__ldg(partials + (int64_t)b * JR + q);
+    }
+    part[w][lane] = t;
+    __syncthreads();
+    if (w == 0 && q < JR) {
+        double u = 0.0;
+#pragma unroll
+        for (int k = 0; k < kReduceWarps; ++k) u += part[k][lane];
+        gB[q] = (float)((scale ? *scale : 1.0) * u);
+    }
 }
 
 cudaError_t launch_grad_project(const float *A, const float *B, const float *dC, int64_t I, int J,
@@ -274,7 +293,7 @@ cudaError_t launch_grad_project(const float *A, const float *B, const float *dC,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int JR = J * R;
-    k_grad_reduce<<<(JR + 255) / 256, 256, 0, st>>>(partials, (int)nblk, JR, scale, gB);
+    k_grad_reduce<<<(JR + 31) / 32, kReduceWarps * 32, 0, st>>>(partials, (int)nblk, JR, scale, gB);
     *launches += 1;
     return cudaGetLastError();
 }
