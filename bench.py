@@ -1182,7 +1182,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             },
             "roofline": {"bound": "hbm", "kernel": f"{dom} pass", "achieved": ach, "peak": peak,
                          "unit": "GB/s", "frac": ach / peak,
-                         "traffic": measured_traffic(f"{workload}|{args.prec}|{args.path}|{dom}"),
+                         # the record covers the default configuration's kernels only
+                         "traffic": (measured_traffic(f"{workload}|{args.prec}|{args.path}|{dom}")
+                                     if args.long_slices == "maps" and args.order == "storage"
+                                     and args.blocked_chains == "on" else None),
                          "peak_source": peak_kind},
             "clocks": clk.summary(),
             "gpu_launches": launches,
