@@ -346,7 +346,8 @@ sft_status sft_set_long_slices(sft_ctx *ctx, int32_t how);
 
 /* Per-mode autotuner of the slice factor pass: times the pass of `mode` with
  * several limits on the length of a crossing slice that is run whole as one
- * chain (2W, 1024 .. 65536, and every crossing slice whole; a longer slice
+ * chain (W, 2W, 1024, 1536, 2048, 3072, .. 49152, 65536, and every crossing
+ * slice whole; W is the factor pass's tile length; a longer slice
  * runs that many nonzeros as a chain and the rest through maps) and keeps the
  * fastest for this mode.  It overrides the tiling's
  * max_direct for that mode until sft_set_slice_tiling is called again.  Every

@@ -742,13 +742,17 @@ sft_status sft_autotune_slices(sft_ctx *c, int32_t mode, const int32_t *const *s
     const bool fibers = fid != nullptr;
     const int64_t W = slice_W(c, nnz);
     // candidate chain lengths (a slice up to it runs whole, a longer one runs
-    // that many positions as its head): the default 2W, powers of two up to
-    // 65536, and every crossing slice whole
-    int64_t cands[16];
+    // that many positions as its head): W and the default 2W, the powers of
+    // two from 1024 to 65536 and the midpoints 1.5 x 2^k between them, and
+    // every crossing slice whole
+    int64_t cands[24];
     int nc = 0;
+    cands[nc++] = W;
     cands[nc++] = 2 * W;
-    for (int64_t L = 1024; L <= 65536; L *= 2)
+    for (int64_t L = 1024; L <= 65536; L *= 2) {
         if (L > 2 * W) cands[nc++] = L;
+        if (L < 65536 && 3 * L / 2 > 2 * W) cands[nc++] = 3 * L / 2;
+    }
     cands[nc++] = (int64_t)1 << 40;
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
