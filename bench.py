@@ -830,6 +830,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
 
         for n in range(N):
             wait_ready(n)
+            if inp.get("expand_rows"):
+                sft.sft_slices_expand_rows(d.ctx, n, sls[n].row_ptr, sls[n].nnz, sls[n].idx[n])
             if timed:
                 a, b = ev_pair("factor")
                 a.record(stream)
@@ -947,8 +949,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
 
         def groups_of(inp):
             if inp["slices"]:
-                # fiber coordinates: only the first nfibers entries are in use
-                gs = [sl.idx + [sl.val, sl.row_ptr]
+                # fiber coordinates: only the first nfibers entries are in use; a
+                # layout's own-mode coordinates are not shipped: the step rebuilds
+                # them from row_ptr on the device (sft_slices_expand_rows)
+                gs = [[t for k, t in enumerate(sl.idx) if k != sl.mode] + [sl.val, sl.row_ptr]
                       + ([sl.fid] + [c[:sl.nfibers] for c in sl.fcoord if c is not None]
                          if sl.fid is not None else [])
                       for sl in inp["slices"]]
@@ -978,6 +982,8 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             return out
 
         sets = [dict(resident), clone_set(resident)]
+        for st_ in sets:
+            st_["expand_rows"] = bool(st_["slices"])
         host = [[t.cpu().pin_memory() for t in g] for g in groups_of(sets[0])]
         h2d = sum(t.numel() * t.element_size() for g in host for t in g)
         hloss = torch.zeros(2, dtype=torch.float64).pin_memory()
@@ -1027,6 +1033,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         et = max_over_ranks(s2.elapsed_time(e2) / 1e3, world)
         e2e = {"value": total_nnz / et, "unit": unit, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 16}
+        if slices:
+            e2e["inputs"] = ("every mode's slice layout without its own-mode coordinates "
+                             "(rebuilt from row_ptr on the device each step), its fiber ids "
+                             "and fiber coordinates, and the test set")
         del sets[1]
 
     # end to end from raw COO: every step copies the raw training and test sets

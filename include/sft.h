@@ -207,6 +207,17 @@ sft_status sft_group_slices(sft_ctx *ctx, int32_t mode, const int32_t *const *id
                             float *out_val, int32_t *out_row_ptr, void *scratch,
                             size_t scratch_bytes);
 
+/* Writes the mode-`mode` coordinate of every position of a slice layout from
+ * its row pointer alone: out[p] = r for row_ptr[r] <= p < row_ptr[r + 1], -1
+ * for positions after the last slice (the bad-data tail of sft_group_slices).
+ * row_ptr: DEVICE, I_mode + 1 int32 as sft_group_slices writes it (row_ptr[0]
+ * = 0, non-decreasing); out: DEVICE, nnz int32, written.  Lets a caller keep
+ * or ship a layout without its mode-`mode` coordinate array (it equals this
+ * expansion) and rebuild it on the device.  Enqueues only; SFT_EINVAL for a
+ * bad mode, nnz or NULL pointers (nnz = 0 does nothing). */
+sft_status sft_slices_expand_rows(sft_ctx *ctx, int32_t mode, const int32_t *row_ptr, int64_t nnz,
+                                  int32_t *out);
+
 /* Bytes of device workspace sft_update_factors_slices needs for a slice layout
  * of nnz nonzeros of mode `mode` under the context's current tiling. */
 size_t sft_slices_workspace_bytes(const sft_ctx *ctx, int32_t mode, int64_t nnz);

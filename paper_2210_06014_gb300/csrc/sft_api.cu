@@ -534,6 +534,19 @@ sft_status sft_group_slices(sft_ctx *c, int32_t mode, const int32_t *const *idx,
     return SFT_OK;
 }
 
+sft_status sft_slices_expand_rows(sft_ctx *c, int32_t mode, const int32_t *row_ptr, int64_t nnz,
+                                  int32_t *out) {
+    if (!c) return SFT_EINVAL;
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    if (nnz < 0 || nnz > 0x7fffffffLL) return fail(c, SFT_EINVAL, "nnz must be in [0, 2^31)");
+    if (nnz == 0) return SFT_OK;
+    if (!row_ptr || !out) return fail(c, SFT_EINVAL, "row_ptr or out is NULL");
+    cudaError_t e = launch_expand_rows(row_ptr, (int32_t)c->dims[mode], nnz, out, c->stream, c->sms);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "row expansion launch");
+    return SFT_OK;
+}
+
 size_t sft_slices_workspace_bytes(const sft_ctx *c, int32_t mode, int64_t nnz) {
     if (!c || mode < 0 || mode >= c->N || nnz < 0) return 0;
     const int64_t W = slice_W(c, nnz);

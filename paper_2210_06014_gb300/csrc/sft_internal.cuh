@@ -93,6 +93,8 @@ size_t slice_workspace_total(int64_t ntiles, int J, int64_t In);
 constexpr bool slice_lane_kernels(int J) { return J <= 16; }
 int slice_tile_length(int64_t nnz, int sms);
 int slice_core_tile_length(int64_t nnz, int sms);
+cudaError_t launch_expand_rows(const int32_t *row_ptr, int32_t In, int64_t nnz, int32_t *out,
+                               cudaStream_t st, int sms);
 cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, float *out_val,
                                 int32_t *row_ptr, unsigned long long *keys, cudaStream_t st,
                                 int sms, int64_t *launches);

@@ -28,7 +28,8 @@ _STATUS = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SF
 EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_factors",
             "sft_update_core", "sft_loss", "sft_loss_async", "sft_predict", "sft_epoch", "sft_sync",
             "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy",
-            "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_workspace_bytes",
+            "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_expand_rows",
+            "sft_slices_workspace_bytes",
             "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling",
             "sft_update_factors_noalloc", "sft_loss_grad_C", "sft_grad_AB",
             "sft_batch_workspace_bytes", "sft_batch_create", "sft_batch_refresh",
@@ -120,6 +121,8 @@ def load(build_if_missing: bool = True):
     lib.sft_group_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, ctypes.POINTER(vp),
                                      vp, vp, vp, ctypes.c_size_t]
     lib.sft_group_slices.restype = ctypes.c_int
+    lib.sft_slices_expand_rows.argtypes = [ctx, i32, vp, i64, vp]
+    lib.sft_slices_expand_rows.restype = ctypes.c_int
     lib.sft_slices_workspace_bytes.argtypes = [ctx, i32, i64]
     lib.sft_slices_workspace_bytes.restype = ctypes.c_size_t
     lib.sft_update_factors_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, f32, f32,
@@ -321,6 +324,13 @@ def sft_destroy(ctx) -> None:
 
 def sft_slices_scratch_bytes(nnz: int) -> int:
     return int(load().sft_slices_scratch_bytes(int(nnz)))
+
+
+def sft_slices_expand_rows(ctx, mode, row_ptr, nnz, out):
+    """out[p] = slice of position p, from row_ptr (device tensors)."""
+    lib = load()
+    _check(lib, ctx, lib.sft_slices_expand_rows(ctx, int(mode), _ptr(row_ptr), int(nnz), _ptr(out)),
+           "sft_slices_expand_rows")
 
 
 def sft_group_slices(ctx, mode, idx, val, perm, nnz, out_idx, out_val, out_row_ptr,

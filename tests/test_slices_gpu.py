@@ -66,6 +66,32 @@ def test_group_slices_layout(sft):
         assert np.array_equal(sl.row_ptr.cpu().numpy(), want_ptr)
 
 
+def test_expand_rows_equals_layout(sft, skewed):
+    """sft_slices_expand_rows rebuilds a layout's own-mode coordinate array from
+    row_ptr: the same int32 array sft_group_slices wrote (Zipf slices of tens of
+    thousands of nonzeros, empty slices, and a layout whose bad coordinates
+    sit after the last slice as -1)."""
+    T = skewed
+    idx, val = to_dev(T)
+    dec = sft.Decomposition(T.A0, T.B0)
+    for n in range(3):
+        sl = dec.slices(n, idx, val, None)
+        out = torch.full_like(sl.idx[n], 12345)
+        sft.sft_slices_expand_rows(dec.ctx, n, sl.row_ptr, sl.nnz, out)
+        dec.sync(60_000)
+        assert torch.equal(out, sl.idx[n]), n
+    # a coordinate out of range: moved behind the last slice by the layout
+    bad = [t.clone() for t in idx]
+    bad[0][::97] = T.spec.dims[0] + 5
+    sl = dec.slices(0, bad, val, None)
+    out = torch.full_like(sl.idx[0], 12345)
+    sft.sft_slices_expand_rows(dec.ctx, 0, sl.row_ptr, sl.nnz, out)
+    with pytest.raises(sft.SftError):
+        dec.sync(60_000)  # the layout build reports the bad coordinates
+    assert torch.equal(out, sl.idx[0])
+    assert int((out == -1).sum()) == len(range(0, T.nnz, 97))
+
+
 @pytest.mark.parametrize("tiling", [(0, 0), (64, -1), (64, 1 << 30), (7, -1), (64, 300), (32, 40)])
 def test_factor_slices_equal_sequential_pass(sft, oracle_mod, tiling):
     """Slice pass == oracle element-by-element pass over the same permutation,
