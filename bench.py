@@ -831,7 +831,11 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         for n in range(N):
             wait_ready(n)
             if inp.get("expand_rows"):
-                sft.sft_slices_expand_rows(d.ctx, n, sls[n].row_ptr, sls[n].nnz, sls[n].idx[n])
+                sl = sls[n]
+                sft.sft_slices_expand_rows(d.ctx, n, sl.row_ptr, sl.nnz, sl.idx[n])
+                if sl.fid is not None:
+                    sft.sft_fibers_expand_coords(d.ctx, n, sl.fid, sl.nnz, sl.fcoord, sl.nfibers,
+                                                 sl.idx)
             if timed:
                 a, b = ev_pair("factor")
                 a.record(stream)
@@ -937,22 +941,25 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     test_rmse = (sse / ntest) ** 0.5 if ntest else None
 
     # end to end through the public API from pinned host buffers: every step's
-    # inputs (the slice layouts with their fiber ids, or the COO set, and the
-    # test set) are copied from pinned host memory inside the timed region and
-    # the loss is read back.  Two device copies of the inputs alternate: step
-    # k+1's copies run on a copy stream while step k computes, each mode's pass
-    # waits only for its own layout, and a copy into a buffer set starts only
-    # after the step that last read it (k-1) has finished.
+    # inputs (what the step's passes read of each slice layout, or the COO set,
+    # and the test set) are copied from pinned host memory inside the timed
+    # region and the loss is read back.  Two device copies of the inputs
+    # alternate: step k+1's copies run on a copy stream while step k computes,
+    # each mode's pass waits only for its own layout, and a copy into a buffer
+    # set starts only after the step that last read it (k-1) has finished.
     e2e = None
     if not args.no_e2e:
         import copy as copy_mod
 
         def groups_of(inp):
             if inp["slices"]:
-                # fiber coordinates: only the first nfibers entries are in use; a
-                # layout's own-mode coordinates are not shipped: the step rebuilds
-                # them from row_ptr on the device (sft_slices_expand_rows)
-                gs = [[t for k, t in enumerate(sl.idx) if k != sl.mode] + [sl.val, sl.row_ptr]
+                # fiber coordinates: only the first nfibers entries are in use.  A
+                # layout's coordinate arrays are not shipped where the step can
+                # rebuild them on the device: its own mode's from row_ptr
+                # (sft_slices_expand_rows), the other modes' from fid and fcoord
+                # (sft_fibers_expand_coords) when the mode has fibers
+                gs = [([t for k, t in enumerate(sl.idx) if k != sl.mode]
+                       if sl.fid is None else []) + [sl.val, sl.row_ptr]
                       + ([sl.fid] + [c[:sl.nfibers] for c in sl.fcoord if c is not None]
                          if sl.fid is not None else [])
                       for sl in inp["slices"]]
@@ -987,31 +994,27 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         host = [[t.cpu().pin_memory() for t in g] for g in groups_of(sets[0])]
         h2d = sum(t.numel() * t.element_size() for g in host for t in g)
         hloss = torch.zeros(2, dtype=torch.float64).pin_memory()
-        # two copy streams take the tensors of each group in turn (more than
-        # one copy engine); a group is ready when both streams have passed it
-        copy_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # one copy stream: a second one gains no bandwidth on the host link,
+        # and with one the sets arrive strictly in step order (step k+1's
+        # copies never compete with step k's); a group is ready at its event
+        copy_stream = torch.cuda.Stream()
         done = [torch.cuda.Event(), torch.cuda.Event()]
 
         def enqueue_copies(k):
             inp = sets[k % 2]
             ready = []
-            for cs in copy_streams:
-                cs.wait_event(done[k % 2])  # the step that last read this set
-            for g_dev, g_host in zip(groups_of(inp), host):
-                for j, (d, h) in enumerate(zip(g_dev, g_host)):
-                    with torch.cuda.stream(copy_streams[j % 2]):
+            copy_stream.wait_event(done[k % 2])  # the step that last read this set
+            with torch.cuda.stream(copy_stream):
+                for g_dev, g_host in zip(groups_of(inp), host):
+                    for d, h in zip(g_dev, g_host):
                         d.copy_(h, non_blocking=True)
-                evs = []
-                for cs in copy_streams:
                     e = torch.cuda.Event()
-                    e.record(cs)
-                    evs.append(e)
-                ready.append(evs)
+                    e.record(copy_stream)
+                    ready.append([e])
             inp["ready"] = ready
 
         def e2e_steps(nsteps):
-            for cs in copy_streams:
-                cs.wait_stream(stream)
+            copy_stream.wait_stream(stream)
             enqueue_copies(0)
             for k in range(nsteps):
                 if k + 1 < nsteps:
@@ -1034,9 +1037,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         e2e = {"value": total_nnz / et, "unit": unit, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 16}
         if slices:
-            e2e["inputs"] = ("every mode's slice layout without its own-mode coordinates "
-                             "(rebuilt from row_ptr on the device each step), its fiber ids "
-                             "and fiber coordinates, and the test set")
+            e2e["inputs"] = ("every mode's slice layout as values, row pointers, fiber ids "
+                             "and fiber coordinates (its coordinate arrays are rebuilt on the "
+                             "device each step: own mode from row_ptr, other modes from the "
+                             "fiber table), and the test set")
         del sets[1]
 
     # end to end from raw COO: every step copies the raw training and test sets

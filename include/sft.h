@@ -268,6 +268,21 @@ sft_status sft_group_fibers(sft_ctx *ctx, int32_t mode, const int32_t *const *si
                             int32_t *fid, int32_t *const *fcoord, int64_t *nfibers, void *scratch,
                             size_t scratch_bytes);
 
+/* Rebuilds the other modes' coordinate arrays of a slice layout from its fiber
+ * table: every position of fiber f holds that fiber's tuple (Eq. (12)), so for
+ * each k != mode, out_idx[k][p] = fcoord[k][fid[p]]; a position whose fid is
+ * not in [0, nfibers) (the -1 that sft_group_fibers gives bad data) gets -1 in
+ * every such k.  fid: DEVICE, nnz int32; fcoord: host array of N device
+ * pointers (the entry for `mode` is ignored), each with nfibers int32; out_idx:
+ * host array of N device pointers (the entry for `mode` is ignored), each nnz
+ * int32, written.  With sft_slices_expand_rows this lets a caller keep or ship
+ * a layout as values, row_ptr, fid and fcoord only and rebuild its coordinate
+ * arrays on the device.  Enqueues only; SFT_EINVAL for a bad mode, nnz or
+ * nfibers (0 <= nfibers <= nnz) or NULL pointers (nnz = 0 does nothing). */
+sft_status sft_fibers_expand_coords(sft_ctx *ctx, int32_t mode, const int32_t *fid, int64_t nnz,
+                                    const int32_t *const *fcoord, int64_t nfibers,
+                                    int32_t *const *out_idx);
+
 /* sft_update_factors_slices with v formed once per fiber: first
  * V[f][0..J_n) = B^(n) p_f for every fiber (V: DEVICE float32, nfibers x J_n,
  * 16-byte aligned, caller-owned), then the element-by-element slice pass reads

@@ -438,6 +438,41 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
     return e;
 }
 
+// The other modes' coordinates of every layout position from its fiber: all
+// positions of fiber f share the tuple fcoord[.][f] (Eq. (12)), so
+// out[q][p] = fcoord[q][fid[p]]; a position outside every fiber (fid outside
+// [0, nfibers): the bad data sft_group_fibers marks -1) gets -1.  fid is read
+// once and each output written once, coalesced; the fcoord reads follow fid,
+// which numbers fibers by first position, so they stay local.
+__global__ void k_fiber_expand(const int32_t *__restrict__ fid, int64_t nnz, int64_t nf,
+                               FiberCoords in, FiberCoordsOut out, int no) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = __ldg(fid + p);
+        const bool ok = 0 <= f && f < nf;
+        for (int q = 0; q < no; ++q) out.c[q][p] = ok ? __ldg(in.c[q] + f) : -1;
+    }
+}
+
+cudaError_t launch_fiber_expand(int N, int mode, const int32_t *fid, int64_t nnz, int64_t nfibers,
+                                const int32_t *const *fcoord, int32_t *const *out_idx,
+                                cudaStream_t st, int sms) {
+    if (nnz <= 0) return cudaSuccess;
+    FiberCoords in{};
+    FiberCoordsOut out{};
+    int no = 0;
+    for (int k = 0; k < N; ++k)
+        if (k != mode) {
+            in.c[no] = fcoord[k];
+            out.c[no] = out_idx[k];
+            ++no;
+        }
+    int64_t b = (nnz + kFibThreads - 1) / kFibThreads;
+    if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;
+    k_fiber_expand<<<(int)b, kFibThreads, 0, st>>>(fid, nnz, nfibers, in, out, no);
+    return cudaGetLastError();
+}
+
 // v is stored as bfloat16 when the cached products are (SFT_BF16) and each lane
 // of a T = R/4 group holds at least two entries of a row (J_n >= R/2, J_n >= 8).
 bool fiber_v_bf16(const PassArgs &a, int J, int R) {

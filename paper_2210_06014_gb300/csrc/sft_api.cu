@@ -644,6 +644,25 @@ sft_status sft_group_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx
     return read_flag(c);
 }
 
+sft_status sft_fibers_expand_coords(sft_ctx *c, int32_t mode, const int32_t *fid, int64_t nnz,
+                                    const int32_t *const *fcoord, int64_t nfibers,
+                                    int32_t *const *out_idx) {
+    if (!c) return SFT_EINVAL;
+    if (mode < 0 || mode >= c->N) return fail(c, SFT_EINVAL, "mode out of range");
+    if (nnz < 0 || nnz > 0x7fffffffLL) return fail(c, SFT_EINVAL, "nnz must be in [0, 2^31)");
+    if (nfibers < 0 || nfibers > nnz) return fail(c, SFT_EINVAL, "nfibers must be in [0, nnz]");
+    if (nnz == 0) return SFT_OK;
+    if (!fid || !fcoord || !out_idx) return fail(c, SFT_EINVAL, "fid, fcoord or out_idx is NULL");
+    for (int k = 0; k < c->N; ++k)
+        if (k != mode && (!fcoord[k] || !out_idx[k]))
+            return fail(c, SFT_EINVAL, "fcoord[k] or out_idx[k] is NULL for a mode k != mode");
+    cudaError_t e = launch_fiber_expand(c->N, mode, fid, nnz, nfibers, fcoord, out_idx, c->stream,
+                                        c->sms);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "fiber coordinate expansion launch");
+    return SFT_OK;
+}
+
 sft_status sft_update_factors_fibers(sft_ctx *c, int32_t mode, const int32_t *const *sidx,
                                      const float *sval, const int32_t *row_ptr, int64_t nnz,
                                      const int32_t *fid, const int32_t *const *fcoord,

@@ -114,6 +114,9 @@ cudaError_t launch_group_fibers(const PassArgs &a, int32_t *fid, int32_t *const 
                                 void *scratch, int64_t *nfibers, cudaStream_t st, int sms,
                                 int64_t *launches);
 bool fiber_v_bf16(const PassArgs &a, int J, int R);
+cudaError_t launch_fiber_expand(int N, int mode, const int32_t *fid, int64_t nnz, int64_t nfibers,
+                                const int32_t *const *fcoord, int32_t *const *out_idx,
+                                cudaStream_t st, int sms);
 cudaError_t launch_factor_fibers(const PassArgs &a, const int32_t *row_ptr, int64_t W, int64_t Lseq,
                                  bool subslices, bool gram, float *maps, const int32_t *fid, const int32_t *const *fcoord,
                                  int64_t nfibers, float *V, int J, int R, const SliceStreams &ss,

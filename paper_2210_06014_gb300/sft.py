@@ -29,6 +29,7 @@ EXPORTED = ["sft_workspace_bytes", "sft_init", "sft_refresh_C", "sft_update_fact
             "sft_update_core", "sft_loss", "sft_loss_async", "sft_predict", "sft_epoch", "sft_sync",
             "sft_set_stream", "sft_last_error", "sft_launch_count", "sft_destroy",
             "sft_slices_scratch_bytes", "sft_group_slices", "sft_slices_expand_rows",
+            "sft_fibers_expand_coords",
             "sft_slices_workspace_bytes",
             "sft_update_factors_slices", "sft_update_core_slices", "sft_set_slice_tiling",
             "sft_update_factors_noalloc", "sft_loss_grad_C", "sft_grad_AB",
@@ -123,6 +124,8 @@ def load(build_if_missing: bool = True):
     lib.sft_group_slices.restype = ctypes.c_int
     lib.sft_slices_expand_rows.argtypes = [ctx, i32, vp, i64, vp]
     lib.sft_slices_expand_rows.restype = ctypes.c_int
+    lib.sft_fibers_expand_coords.argtypes = [ctx, i32, vp, i64, vp, i64, vp]
+    lib.sft_fibers_expand_coords.restype = ctypes.c_int
     lib.sft_slices_workspace_bytes.argtypes = [ctx, i32, i64]
     lib.sft_slices_workspace_bytes.restype = ctypes.c_size_t
     lib.sft_update_factors_slices.argtypes = [ctx, i32, ctypes.POINTER(vp), vp, vp, i64, f32, f32,
@@ -331,6 +334,16 @@ def sft_slices_expand_rows(ctx, mode, row_ptr, nnz, out):
     lib = load()
     _check(lib, ctx, lib.sft_slices_expand_rows(ctx, int(mode), _ptr(row_ptr), int(nnz), _ptr(out)),
            "sft_slices_expand_rows")
+
+
+def sft_fibers_expand_coords(ctx, mode, fid, nnz, fcoord, nfibers, out_idx):
+    """out_idx[k][p] = fcoord[k][fid[p]] for k != mode (device tensors; the
+    entries for `mode` may be None)."""
+    lib = load()
+    _check(lib, ctx, lib.sft_fibers_expand_coords(ctx, int(mode), _ptr(fid), int(nnz),
+                                                  _ptr_array(fcoord), int(nfibers),
+                                                  _ptr_array(out_idx)),
+           "sft_fibers_expand_coords")
 
 
 def sft_group_slices(ctx, mode, idx, val, perm, nnz, out_idx, out_val, out_row_ptr,

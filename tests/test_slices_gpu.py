@@ -92,6 +92,38 @@ def test_expand_rows_equals_layout(sft, skewed):
     assert int((out == -1).sum()) == len(range(0, T.nnz, 97))
 
 
+def test_fibers_expand_coords_equals_layout(sft, skewed):
+    """sft_fibers_expand_coords rebuilds a layout's other-mode coordinate arrays
+    from fid and fcoord: the same int32 arrays sft_group_slices wrote, for every
+    mode of a Zipf tensor; a position outside every fiber (fid -1, as
+    sft_group_fibers marks bad data, or fid >= nfibers) gets -1."""
+    T = skewed
+    idx, val = to_dev(T)
+    N = len(idx)
+    dec = sft.Decomposition(T.A0, T.B0)
+    for n in range(N):
+        sl = dec.slices(n, idx, val, None)
+        sl.build_fibers(dec)
+        out = [None if k == n else torch.full_like(sl.idx[k], 12345) for k in range(N)]
+        sft.sft_fibers_expand_coords(dec.ctx, n, sl.fid, sl.nnz, sl.fcoord, sl.nfibers, out)
+        dec.sync(60_000)
+        for k in range(N):
+            if k != n:
+                assert torch.equal(out[k], sl.idx[k]), (n, k)
+    # positions outside every fiber
+    fid = sl.fid.clone()
+    fid[::89] = -1
+    fid[5::131] = sl.nfibers
+    out = [torch.full_like(sl.idx[k], 12345) for k in range(N - 1)] + [None]
+    sft.sft_fibers_expand_coords(dec.ctx, N - 1, fid, sl.nnz, sl.fcoord, sl.nfibers, out)
+    dec.sync(60_000)
+    badpos = (fid < 0) | (fid >= sl.nfibers)
+    assert int(badpos.sum()) > 0
+    for k in range(N - 1):
+        assert torch.equal(out[k][~badpos], sl.idx[k][~badpos]), k
+        assert bool((out[k][badpos] == -1).all()), k
+
+
 @pytest.mark.parametrize("tiling", [(0, 0), (64, -1), (64, 1 << 30), (7, -1), (64, 300), (32, 40)])
 def test_factor_slices_equal_sequential_pass(sft, oracle_mod, tiling):
     """Slice pass == oracle element-by-element pass over the same permutation,
@@ -546,6 +578,37 @@ def test_fiber_core_pass_equals_row_pass(sft, case):
         outs.append([b.clone() for b in dec.B])
     for n, (a, b) in enumerate(zip(*outs)):
         assert torch.equal(a, b), (case, n, (a - b).abs().max().item())
+
+
+@pytest.mark.parametrize("tiling", [(0, 0), (64, -1), (64, 1 << 30), (0, 8192)])
+def test_fiber_passes_read_no_other_coordinates(sft, skewed, tiling):
+    """With fiber tables for both passes, a mode's factor and core passes read
+    the other modes only through fid / fcoord (Eq. (12)-(13)): replacing the
+    layout's other-mode coordinate arrays by different in-range values leaves
+    every bit of A and B unchanged, on the tiled, map, chain and blocked-chain
+    paths."""
+    T = skewed
+    idx, val = to_dev(T)
+    N = len(idx)
+    outs = []
+    for scramble in (False, True):
+        dec = sft.Decomposition(T.A0, T.B0)
+        dec.set_slice_tiling(*tiling)
+        for n in range(N):
+            sl = dec.slices(n, idx, val, None)
+            sl.build_fibers(dec, core=True)
+            if scramble:
+                for k in range(N):
+                    if k != n:
+                        sl.idx[k].copy_(torch.roll(sl.idx[k], 7919))
+            dec.update_factors_slices(sl, lr=0.01, lam=0.01)
+            dec.refresh(n)
+            dec.update_core_slices(sl, lr=0.01, lam=0.01)
+            dec.refresh(n)
+        dec.sync(60_000)
+        outs.append([t.clone() for t in list(dec.A) + list(dec.B)])
+    for q, (a, b) in enumerate(zip(*outs)):
+        assert torch.equal(a, b), (tiling, q, (a - b).abs().max().item())
 
 
 @pytest.mark.parametrize("fibers", [False, True])
