@@ -274,25 +274,31 @@ cudaError_t launch_group_slices(const PassArgs &a, int32_t *const *out_idx, floa
 
 
 // The mode-n coordinates of a slice layout from its row_ptr alone (every
-// position of slice r holds r): each thread takes 8 consecutive positions,
-// finds the slice of the first by binary search and walks on.
-constexpr int kExpandPer = 8;
+// position of slice r holds r).  A warp takes a span of 32 x kExpandPer
+// consecutive positions; lane l writes positions l, l + 32, ... of it (stores
+// coalesced across the warp), finds the slice of its first position by binary
+// search and then only steps r forward past the slice ends it crosses.
+constexpr int kExpandPer = 64;
 
 __global__ void k_expand_rows(const int32_t *__restrict__ row_ptr, int32_t In, int64_t nnz,
                               int32_t *__restrict__ out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kExpandPer;
-    for (int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kExpandPer; p0 < nnz;
-         p0 += stride) {
-        // last r with row_ptr[r] <= p0 (row_ptr is non-decreasing, row_ptr[0] = 0)
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int64_t kSpan = 32 * kExpandPer;
+    for (int64_t c0 = warp * kSpan; c0 < nnz; c0 += nwarps * kSpan) {
+        const int64_t c1 = min(nnz, c0 + kSpan);
+        int64_t p = c0 + lane;
+        if (p >= c1) continue;
+        // last r with row_ptr[r] <= p (row_ptr is non-decreasing, row_ptr[0] = 0)
         int32_t lo = 0, hi = In;
         while (lo < hi) {
             const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
-            if (__ldg(row_ptr + mid) <= p0) lo = mid; else hi = mid - 1;
+            if (__ldg(row_ptr + mid) <= p) lo = mid; else hi = mid - 1;
         }
         int32_t r = lo;
         int64_t next = r < In ? __ldg(row_ptr + r + 1) : nnz;
-        const int64_t p1 = min(nnz, p0 + kExpandPer);
-        for (int64_t p = p0; p < p1; ++p) {
+        for (; p < c1; p += 32) {
             while (p >= next && r < In) {
                 ++r;
                 next = r < In ? __ldg(row_ptr + r + 1) : nnz;
@@ -305,7 +311,8 @@ __global__ void k_expand_rows(const int32_t *__restrict__ row_ptr, int32_t In, i
 cudaError_t launch_expand_rows(const int32_t *row_ptr, int32_t In, int64_t nnz, int32_t *out,
                                cudaStream_t st, int sms) {
     if (nnz <= 0) return cudaSuccess;
-    int64_t b = (nnz + 256 * kExpandPer - 1) / (256 * kExpandPer);
+    const int64_t span = 32 * kExpandPer;
+    int64_t b = ((nnz + span - 1) / span + 7) / 8;  // 8 warps per block
     if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;
     k_expand_rows<<<(int)b, 256, 0, st>>>(row_ptr, In, nnz, out);
     return cudaGetLastError();
