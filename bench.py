@@ -12,9 +12,11 @@ slices of Section "Tensor Storage Format", built once before timing) and the
 factor pass runs every slice element by element (Algorithm 4 order); with
 --path coo the factor pass is the Hogwild COO kernel instead.
 value = training nonzeros / epoch time.  Inputs live in HBM (several GB,
-larger than L2); `e2e` repeats the step with the step's inputs (the slice
-layouts and the test set) copied from pinned host memory inside the timed
-region and the loss read back.
+larger than L2); `e2e` repeats the step with the step's inputs (each slice
+layout as values, row pointers, fiber ids and fiber coordinates, whose
+coordinate arrays the step rebuilds on the device, and the test set) copied
+from pinned host memory inside the timed region and the loss read back;
+`e2e_raw` starts from the raw COO and also builds every layout each step.
 
 --impl reference times the FP64 CPU oracle on a bounded prefix of the same
 workload (the only CPU code this script runs).
