@@ -215,7 +215,8 @@ __device__ __forceinline__ bool fiber_rows(const PassArgs &a, const int32_t (&ci
     ok = ok && !bad;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (ok && q < a.N - 1) ? ldC_raw<CT>(a.oC[q], (int64_t)ci[q] * R + 4 * sub)
+        w.r[q] = (ok && q < a.N - 1) ? ldC_raw_l1<CT>(a.oC[q], (int64_t)ci[q] * R + 4 * sub,
+                                                       (a.ol1 >> q) & 1u)
                                      : c_one<CT>();
     return ok;
 }

@@ -39,7 +39,21 @@ struct PassArgs {
     const int32_t *oidx[kMaxOrder];
     const float *oC[kMaxOrder];
     int32_t odims[kMaxOrder];
+    // bit q: other mode q's cached-product table is at most kL1TableBytes and
+    // its rows are gathered through L1; the rows of larger tables are read
+    // from L2 only
+    uint32_t ol1;
 };
+
+// The slice walks and the fiber table gather one random cached row per other
+// mode and position.  A table larger than this gets little from L1 (its rows
+// are rarely reused before eviction), so its rows are loaded with
+// ld.global.cg, which measured faster on such tables than the
+// non-coherent L1 path; tables this small stay on the L1 path.
+#ifndef SFT_L1_TABLE_BYTES
+#define SFT_L1_TABLE_BYTES (64 * 1024)
+#endif
+constexpr int64_t kL1TableBytes = SFT_L1_TABLE_BYTES;
 
 // Workspace pieces used by the deterministic factor path.
 struct DetFactorWs {
@@ -213,6 +227,28 @@ __device__ __forceinline__ float4 ldC_raw<float>(const float *base, int64_t off)
 template <>
 __device__ __forceinline__ uint2 ldC_raw<__nv_bfloat16>(const float *base, int64_t off) {
     return __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + off));
+}
+
+#ifndef SFT_L1_HINT
+#define SFT_L1_HINT 1
+#endif
+
+// ldC_raw with the table's cache policy: l1 = through L1 (ld.global.nc), else
+// L2 only (ld.global.cg).  The same bits either way.
+template <typename CT>
+__device__ __forceinline__ typename CRaw<CT>::type ldC_raw_l1(const float *base, int64_t off,
+                                                              bool l1);
+
+template <>
+__device__ __forceinline__ float4 ldC_raw_l1<float>(const float *base, int64_t off, bool l1) {
+    const float4 *p = reinterpret_cast<const float4 *>(base + off);
+    return (l1 || !SFT_L1_HINT) ? __ldg(p) : __ldcg(p);
+}
+
+template <>
+__device__ __forceinline__ uint2 ldC_raw_l1<__nv_bfloat16>(const float *base, int64_t off, bool l1) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + off);
+    return (l1 || !SFT_L1_HINT) ? __ldg(p) : __ldcg(p);
 }
 
 template <typename CT>

@@ -12,7 +12,9 @@
 // for J <= 16; J = 32 keeps more registers.
 #define SFT_DIRECT_MINB 2
 #define SFT_MAPS_MINB (J >= 32 ? 1 : 2)
+#ifndef SFT_CORE_MINB
 #define SFT_CORE_MINB (J >= 32 ? 2 : 4)
+#endif
 #ifndef SFT_MAP_RING_D
 #define SFT_MAP_RING_D 4
 #endif
@@ -73,7 +75,8 @@ __device__ __forceinline__ void load_rows(const PassArgs &a, const Sample<NO> &c
     ok = c.valid && !bad;
 #pragma unroll
     for (int q = 0; q < NO; ++q)
-        w.r[q] = (ok && q < a.N - 1) ? ldC_raw<CT>(a.oC[q], (int64_t)c.i[q] * R + 4 * sub)
+        w.r[q] = (ok && q < a.N - 1) ? ldC_raw_l1<CT>(a.oC[q], (int64_t)c.i[q] * R + 4 * sub,
+                                                       (a.ol1 >> q) & 1u)
                                      : c_one<CT>();
 }
 
