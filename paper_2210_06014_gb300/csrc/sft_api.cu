@@ -159,7 +159,7 @@ PassArgs pass_args(const sft_ctx *c, int mode, const int32_t *const *idx, const 
             a.oidx[q] = idx[k];
             a.oC[q] = c->C[k];
             a.odims[q] = (int32_t)c->dims[k];
-            if (c->dims[k] * c->R * (c->cbf16 ? 2 : 4) <= kL1TableBytes) a.ol1 |= 1u << q;
+            if (!l2_only_rows(c->dims[k], c->R, c->cbf16)) a.ol1 |= 1u << q;
             ++q;
         }
     }

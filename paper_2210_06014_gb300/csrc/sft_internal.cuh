@@ -46,14 +46,19 @@ struct PassArgs {
 };
 
 // The slice walks and the fiber table gather one random cached row per other
-// mode and position.  A table larger than this gets little from L1 (its rows
-// are rarely reused before eviction), so its rows are loaded with
-// ld.global.cg, which measured faster on such tables than the
-// non-coherent L1 path; tables this small stay on the L1 path.
+// mode and position.  Rows of float32 tables with R <= 16 (64-byte rows)
+// larger than kL1TableBytes are loaded with ld.global.cg (L2 only), which
+// measured faster there than the non-coherent L1 path; bfloat16 tables,
+// 128-byte rows (R = 32) and small tables measured faster on the L1 path and
+// stay on it.
 #ifndef SFT_L1_TABLE_BYTES
 #define SFT_L1_TABLE_BYTES (64 * 1024)
 #endif
 constexpr int64_t kL1TableBytes = SFT_L1_TABLE_BYTES;
+
+inline bool l2_only_rows(int64_t rows, int R, int cbf16) {
+    return !cbf16 && R <= 16 && rows * R * 4 > kL1TableBytes;
+}
 
 // Workspace pieces used by the deterministic factor path.
 struct DetFactorWs {
