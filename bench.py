@@ -1002,10 +1002,21 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         copy_stream = torch.cuda.Stream()
         done = [torch.cuda.Event(), torch.cuda.Event()]
 
+        # timing events of the timed run: per set, its copies on the copy
+        # stream; per step, its work on the compute stream (reported as medians
+        # so that a slow host link shows as such)
+        spans = {"copy": [], "step": []}
+
+        def span(kind, st):
+            a = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            spans[kind].append(a)
+
         def enqueue_copies(k):
             inp = sets[k % 2]
             ready = []
             copy_stream.wait_event(done[k % 2])  # the step that last read this set
+            span("copy", copy_stream)
             with torch.cuda.stream(copy_stream):
                 for g_dev, g_host in zip(groups_of(inp), host):
                     for d, h in zip(g_dev, g_host):
@@ -1013,6 +1024,7 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                     e = torch.cuda.Event()
                     e.record(copy_stream)
                     ready.append([e])
+            span("copy", copy_stream)
             inp["ready"] = ready
 
         def e2e_steps(nsteps):
@@ -1021,7 +1033,9 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
             for k in range(nsteps):
                 if k + 1 < nsteps:
                     enqueue_copies(k + 1)
+                span("step", stream)
                 step(False, sets[k % 2])
+                span("step", stream)
                 done[k % 2].record(stream)
                 hloss.copy_(loss_out, non_blocking=True)
 
@@ -1031,13 +1045,24 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
         torch.cuda.synchronize()
         barrier(world)
         s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        spans["copy"].clear()
+        spans["step"].clear()
         s2.record(stream)
         e2e_steps(args.steps)
         e2.record(stream)
         torch.cuda.synchronize()
         et = max_over_ranks(s2.elapsed_time(e2) / 1e3, world)
+
+        def median_ms(evs):
+            xs = [a.elapsed_time(b) for a, b in zip(evs[0::2], evs[1::2])]
+            return statistics.median(xs) if xs else None
+
+        copy_ms = median_ms(spans["copy"])
         e2e = {"value": total_nnz / et, "unit": unit, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": 16}
+               "d2h_bytes_per_step": 16,
+               "copy_ms_per_step": copy_ms,
+               "h2d_gbs": h2d / copy_ms / 1e6 if copy_ms else None,
+               "compute_ms_per_step": median_ms(spans["step"])}
         if slices:
             e2e["inputs"] = ("every mode's slice layout as values, row pointers, fiber ids "
                              "and fiber coordinates (its coordinate arrays are rebuilt on the "
