@@ -264,6 +264,54 @@ def algorithmic_bytes(N, J, R, path="coo", rows_per_nnz=1.0, c_bytes=4):
     return coo + gather + 2 * J * 4 * f, coo + gather + J * 4 * f
 
 
+# ----------------------------------------------------------------------------- e2e inputs
+
+
+def e2e_groups(inp, N: int):
+    """The device tensors an end-to-end step copies from the host, one group per
+    mode and one for the test set (a mode's pass waits only for its group).
+    A slice layout ships its values, row_ptr and, with fibers, its fiber ids
+    and the first nfibers entries of its fiber coordinates.  Its coordinate
+    arrays are not shipped where the step rebuilds them on the device: the
+    own mode's from row_ptr (sft_slices_expand_rows), the other modes' from
+    fid and fcoord (sft_fibers_expand_coords) when the mode has fibers.  On
+    the COO path the whole set is the first group."""
+    if inp["slices"]:
+        gs = [([t for k, t in enumerate(sl.idx) if k != sl.mode]
+               if sl.fid is None else []) + [sl.val, sl.row_ptr]
+              + ([sl.fid] + [c[:sl.nfibers] for c in sl.fcoord if c is not None]
+                 if sl.fid is not None else [])
+              for sl in inp["slices"]]
+    else:
+        gs = [list(inp["idx"]) + [inp["val"]]] + [[] for _ in range(N - 1)]
+    return gs + [list(inp["tidx"]) + [inp["tval"]]]
+
+
+def e2e_clone_set(inp):
+    """A second set of device buffers shaped like `inp` (the e2e steps
+    alternate between two, so that step k+1's copies overlap step k)."""
+    import copy as copy_mod
+    out = dict(inp)
+    if inp["slices"]:
+        sl2 = []
+        for sl in inp["slices"]:
+            c = copy_mod.copy(sl)
+            c.idx = [torch.empty_like(t) for t in sl.idx]
+            c.val = torch.empty_like(sl.val)
+            c.row_ptr = torch.empty_like(sl.row_ptr)
+            if sl.fid is not None:
+                c.fid = torch.empty_like(sl.fid)
+                c.fcoord = [None if t is None else torch.empty_like(t) for t in sl.fcoord]
+            sl2.append(c)
+        out["slices"] = sl2
+    else:
+        out["idx"] = [torch.empty_like(t) for t in inp["idx"]]
+        out["val"] = torch.empty_like(inp["val"])
+    out["tidx"] = [torch.empty_like(t) for t in inp["tidx"]]
+    out["tval"] = torch.empty_like(inp["tval"])
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 
@@ -951,46 +999,10 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
     # set starts only after the step that last read it (k-1) has finished.
     e2e = None
     if not args.no_e2e:
-        import copy as copy_mod
-
         def groups_of(inp):
-            if inp["slices"]:
-                # fiber coordinates: only the first nfibers entries are in use.  A
-                # layout's coordinate arrays are not shipped where the step can
-                # rebuild them on the device: its own mode's from row_ptr
-                # (sft_slices_expand_rows), the other modes' from fid and fcoord
-                # (sft_fibers_expand_coords) when the mode has fibers
-                gs = [([t for k, t in enumerate(sl.idx) if k != sl.mode]
-                       if sl.fid is None else []) + [sl.val, sl.row_ptr]
-                      + ([sl.fid] + [c[:sl.nfibers] for c in sl.fcoord if c is not None]
-                         if sl.fid is not None else [])
-                      for sl in inp["slices"]]
-            else:
-                gs = [list(inp["idx"]) + [inp["val"]]] + [[] for _ in range(N - 1)]
-            return gs + [list(inp["tidx"]) + [inp["tval"]]]
+            return e2e_groups(inp, N)
 
-        def clone_set(inp):
-            out = dict(inp)
-            if inp["slices"]:
-                sl2 = []
-                for sl in inp["slices"]:
-                    c = copy_mod.copy(sl)
-                    c.idx = [torch.empty_like(t) for t in sl.idx]
-                    c.val = torch.empty_like(sl.val)
-                    c.row_ptr = torch.empty_like(sl.row_ptr)
-                    if sl.fid is not None:
-                        c.fid = torch.empty_like(sl.fid)
-                        c.fcoord = [None if t is None else torch.empty_like(t) for t in sl.fcoord]
-                    sl2.append(c)
-                out["slices"] = sl2
-            else:
-                out["idx"] = [torch.empty_like(t) for t in inp["idx"]]
-                out["val"] = torch.empty_like(inp["val"])
-            out["tidx"] = [torch.empty_like(t) for t in inp["tidx"]]
-            out["tval"] = torch.empty_like(inp["tval"])
-            return out
-
-        sets = [dict(resident), clone_set(resident)]
+        sets = [dict(resident), e2e_clone_set(resident)]
         for st_ in sets:
             st_["expand_rows"] = bool(st_["slices"])
         host = [[t.cpu().pin_memory() for t in g] for g in groups_of(sets[0])]

@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the measured-traffic record (it is
-reported only while the digest of the listed sources still matches) and the
-clock sampler's selection of the samples inside the timed region."""
+reported only while the digest of the listed sources still matches), the
+clock sampler's selection of the samples inside the timed region, and the
+choice of arrays the end-to-end step copies from the host."""
 import json
 import os
 import sys
@@ -82,3 +83,67 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch):
     with bench.ClockSampler(0) as c:
         pass
     assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+class _Layout:
+    """The attributes of a slice layout that the end-to-end copies use."""
+
+    def __init__(self, mode, N, nnz, nfibers=None):
+        import torch
+        self.mode = mode
+        self.nnz = nnz
+        self.idx = [torch.arange(nnz, dtype=torch.int32) + 100 * k for k in range(N)]
+        self.val = torch.rand(nnz)
+        self.row_ptr = torch.arange(nnz + 1, dtype=torch.int32)
+        self.nfibers = nfibers or 0
+        if nfibers is None:
+            self.fid = self.fcoord = None
+        else:
+            self.fid = torch.zeros(nnz, dtype=torch.int32)
+            self.fcoord = [None if k == mode else torch.arange(nnz, dtype=torch.int32)
+                           for k in range(N)]
+
+
+def _inputs(layouts, N):
+    import torch
+    return {"slices": layouts, "tidx": [torch.zeros(5, dtype=torch.int32) for _ in range(N)],
+            "tval": torch.zeros(5), "ready": None}
+
+
+def test_e2e_ships_compact_layouts():
+    """A mode with fibers ships values, row_ptr, fid and nfibers entries of its
+    fiber coordinates (no coordinate arrays: the step rebuilds them); a mode
+    without fibers ships the other modes' coordinates too; never the own
+    mode's coordinates; the test set is the last group."""
+    N, nnz = 3, 40
+    lays = [_Layout(0, N, nnz, nfibers=7), _Layout(1, N, nnz), _Layout(2, N, nnz, nfibers=9)]
+    inp = _inputs(lays, N)
+    groups = bench.e2e_groups(inp, N)
+    assert len(groups) == N + 1
+    g0 = groups[0]
+    assert g0[0] is lays[0].val and g0[1] is lays[0].row_ptr and g0[2] is lays[0].fid
+    assert [t.numel() for t in g0[3:]] == [7, 7] and len(g0) == 5
+    g1 = groups[1]
+    assert g1[0] is lays[1].idx[0] and g1[1] is lays[1].idx[2]
+    assert g1[2] is lays[1].val and g1[3] is lays[1].row_ptr and len(g1) == 4
+    assert [t.numel() for t in groups[2][3:]] == [9, 9]
+    for g, sl in zip(groups, lays):
+        assert all(t is not sl.idx[sl.mode] for t in g)
+    assert groups[N][-1] is inp["tval"] and len(groups[N]) == N + 1
+
+
+def test_e2e_second_set_owns_its_buffers():
+    """The second buffer set has fresh tensors of the same shapes for every
+    shipped or rebuilt array, and shares nothing written by a step's copies."""
+    N, nnz = 3, 40
+    lays = [_Layout(0, N, nnz, nfibers=7), _Layout(1, N, nnz), _Layout(2, N, nnz, nfibers=9)]
+    inp = _inputs(lays, N)
+    two = bench.e2e_clone_set(inp)
+    ga, gb = bench.e2e_groups(inp, N), bench.e2e_groups(two, N)
+    assert [[tuple(t.shape) for t in g] for g in ga] == [[tuple(t.shape) for t in g] for g in gb]
+    for x, y in zip(ga, gb):
+        for a, b in zip(x, y):
+            assert a.data_ptr() != b.data_ptr()
+    for a, b in zip(lays, two["slices"]):
+        assert b.mode == a.mode and b.nfibers == a.nfibers
+        assert all(p.data_ptr() != q.data_ptr() for p, q in zip(a.idx, b.idx))
