@@ -1080,6 +1080,9 @@ def run_sgd(args, world, rank, sft, T, spec, metric, unit, gen_s, lr, print_line
                              "and fiber coordinates (its coordinate arrays are rebuilt on the "
                              "device each step: own mode from row_ptr, other modes from the "
                              "fiber table), and the test set")
+            if any(sl.fid is None for sl in slices):
+                e2e["inputs"] += ("; a mode without fibers ships its values, row pointers "
+                                  "and other modes' coordinates instead")
         del sets[1]
 
     # end to end from raw COO: every step copies the raw training and test sets
