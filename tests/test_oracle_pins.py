@@ -10,6 +10,8 @@ the model, and recovery of a planted low-rank tensor.
 """
 import itertools
 
+import os
+
 import numpy as np
 import pytest
 
@@ -80,11 +82,41 @@ def unfold(X, n):
 # ----------------------------------------------------------------------------- generator pins
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_rows(name):
+    """Non-comment rows of a fixture under tests/golden/, split on whitespace."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
 def test_splitmix64_reference_outputs():
-    """SplitMix64 with state 0: the first outputs of the published generator."""
+    """SplitMix64 with state 0: the first outputs of the published generator
+    (tests/golden/splitmix64_state0.txt)."""
     from paper_2210_06014_gb300 import synth
-    got = [int(v) & ((1 << 64) - 1) for v in synth.bits(0, 3).tolist()]
-    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    want = [int(r[0], 16) for r in golden_rows("splitmix64_state0.txt")]
+    got = [int(v) & ((1 << 64) - 1) for v in synth.bits(0, len(want)).tolist()]
+    assert got == want
+
+
+def test_ratings_stand_in_has_the_netflix_shape():
+    """The synthetic ratings tensor stands in for the paper's Netflix tensor
+    (table "Real World Datasets", tests/golden/real_world_datasets.txt): mode
+    lengths within 1 %, total nonzeros within 1 % of |Omega| + |Gamma|, and
+    integer ratings inside the printed value range."""
+    from paper_2210_06014_gb300 import synth
+    rows = {r[0]: r[1:] for r in golden_rows("real_world_datasets.txt")}
+    I1, I2, I3, omega, gamma = (int(x) for x in rows["netflix"][:5])
+    vmax, vmin = float(rows["netflix"][5]), float(rows["netflix"][6])
+    spec = synth.spec_ratings()
+    for got, want in zip(spec.dims, (I1, I2, I3)):
+        assert abs(got - want) <= 0.01 * want, (got, want)
+    assert abs(spec.nnz - (omega + gamma)) <= 0.01 * (omega + gamma)
+    T = synth.make_tensor(synth.spec_ratings(nnz=200_000))
+    vals = np.concatenate([T.val.numpy(), T.test_val.numpy()])
+    assert vals.min() >= vmin and vals.max() <= vmax
+    assert np.all(vals == np.round(vals))
 
 
 def test_generator_distinct_and_in_range():
