@@ -48,6 +48,8 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     assert lib.sft_update_factors(None, 0, None, None, None, 0, 1, 0.0, 0.0) == sft.SFT_EINVAL
     assert lib.sft_update_core(None, 0, None, None, None, 0, 1, 0.0, 0.0) == sft.SFT_EINVAL
     assert lib.sft_sync(None, 0) == sft.SFT_EINVAL
+    assert lib.sft_slices_expand_rows(None, 0, None, 1, None) == sft.SFT_EINVAL
+    assert lib.sft_fibers_expand_coords(None, 0, None, 1, None, 1, None) == sft.SFT_EINVAL
     assert lib.sft_last_error(None) == b"null context"
     lib.sft_destroy(None)
 
